@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark: PP-GMRES solve time on 2-D convection-diffusion, 1000 x 1000.
+
+Workload (one "step" = the whole hot path on one system): build the degree-40
+GMRES polynomial from a seeded Gaussian v0 (device Arnoldi + host harmonic
+Ritz / Leja / root adding), then PP(40+k)-GMRES(50) to true relative
+residual 1e-10 (phi(A) by Algorithm 1 each iteration, x += p(A) y by
+Algorithm 3 each restart).  n = 1,000,000, nnz = 4,996,000, FP64, beta*h = 1.
+Inputs are resident in HBM when the timed region starts; L2 is flushed
+(a 512 MB write) between timed steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
+
+Multi-GPU: every rank solves its own copy (replicas; the method has no
+exchange step here), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cd2d_1000"
+METRIC = ("PP-GMRES solve time to rel-res 1e-10 (build_poly d=40 + PP(40+k)-GMRES(50)), "
+          "2-D convection-diffusion 1000x1000; p(A)v GB/s vs HBM")
+UNIT = "ms"
+# Outer iterations and restarts of this workload as measured on one GB300
+# (device iteration counts match the oracle within 2 at reduced sizes); used
+# only to extrapolate the CPU oracle's per-iteration time to a full solve.
+ITERS_REF = None
+CYCLES_REF = None
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("spmv_root.cu", "ppg_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1911_07065_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the SpMV-root kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "spmv_root_cd2d_1000.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != _kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_phi_real"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """Sample nvidia-smi during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+                   samples=len(rows))
+        return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (also the reference arm)
+# ---------------------------------------------------------------------------
+
+
+def oracle_sample(n_iters: int = 2):
+    """Time the oracle on a bounded sample of the workload: the full
+    polynomial construction, then the first n_iters outer PP-GMRES steps
+    (each d SpMVs of Algorithm 1 + CGS2 + Givens) and one restart update
+    (Algorithm 3 + true residual).  Returns a dict of per-part seconds."""
+    import numpy as np
+    import synth
+    from oracle import gmres, poly
+
+    P = synth.problem(WORKLOAD)
+    As = P.A.to_scipy()
+    t0 = time.perf_counter()
+    pp = poly.build_poly(As, P.d, P.v0)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, st = gmres.pp_gmres(As, pp.roots, P.b, n_iters, 1e-300, max_cycles=1)
+    t_cyc = time.perf_counter() - t0
+    # split the cycle time into per-iteration and end-of-cycle parts
+    t0 = time.perf_counter()
+    u = np.random.default_rng(0).standard_normal(P.A.n)
+    x = poly.apply_p(As, pp.roots, u)
+    r = P.b - As @ x
+    float(np.linalg.norm(r))
+    t_end = time.perf_counter() - t0
+    t_iter = max(t_cyc - t_end, 0.0) / n_iters
+    return {"t_build": t_build, "t_iter": t_iter, "t_end": t_end, "n_iters": n_iters,
+            "degree": int(pp.roots.size)}
+
+
+def _run_oracle_subprocess(n_iters):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                        str(n_iters)], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _extrapolate(s, iters, cycles):
+    return 1e3 * (s["t_build"] + iters * s["t_iter"] + cycles * s["t_end"])
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers
+# ---------------------------------------------------------------------------
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, local, world
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world <= 1:
+        return
+    import torch.distributed as dist
+    if device is not None and dist.get_backend() == "nccl":
+        dist.barrier(device_ids=[device.index])
+    else:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = _run_oracle_subprocess(args.oracle_iters)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            steps.append((s, dt))
+    iters = ITERS_REF or args.ref_iters
+    cycles = CYCLES_REF or args.ref_cycles
+    vals = [_extrapolate(s, iters, cycles) for s, _ in steps]
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(v, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 1000000, "nnz": 4996000, "d": 40, "m": 50,
+                   "tol": 1e-10, "extrapolated": True},
+        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle build_poly(d=40) + %d PP-GMRES iterations + one "
+                                   "restart update per step, extrapolated to %d iterations / "
+                                   "%d restarts" % (args.oracle_iters, iters, cycles)},
+        "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+    import synth
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    P = synth.problem(WORKLOAD)
+    A = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
+    b = torch.from_numpy(P.b).to(device)
+    v0 = torch.from_numpy(P.v0).to(device)
+    x = torch.empty_like(b)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        R = ppg.build_poly(A, P.d, v0)
+        _, st = ppg.solve(A, b, P.m, P.tol, roots=R, timing=True, out=x)
+        return R, st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    per_step = []
+    stats = []
+    launches0 = ppg.lib.ppg_launch_count()
+    barrier(world, device)
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        per_step.append(e0.elapsed_time(e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world, device)
+    launches = ppg.lib.ppg_launch_count() - launches0
+    ms_local = float(np.mean(per_step))
+    ms = reduce_max(ms_local, world, device)
+
+    st = stats[-1]
+    rel = float(np.linalg.norm(P.b - P.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(P.b))
+    poly_bytes = sum(s["poly_bytes"] for s in stats)
+    poly_ms = sum(s["poly_ms"] for s in stats)
+    poly_launches = sum(s["poly_launches"] for s in stats)
+    achieved = poly_bytes / (poly_ms * 1e-3) / 1e9 if poly_ms > 0 else None
+    peak, peak_kind = _peaks()
+    traffic = _ncu_traffic()
+
+    # end to end through the public API from host arrays
+    e2e_ms = []
+    h2d = P.A.rowptr.nbytes + P.A.colind.nbytes + P.A.vals.nbytes + P.b.nbytes + P.v0.nbytes
+    d2h = P.b.nbytes
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ppg.solve_host(P.A.rowptr, P.A.colind, P.A.vals, P.b, P.v0, P.d, P.m, P.tol,
+                       device=device)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e = reduce_max(float(np.mean(e2e_ms)), world, device)
+
+    # plain GMRES(50) on the same GPU, capped
+    plain = None
+    if not args.no_plain:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xp, sp = ppg.solve(A, b, P.m, P.tol, roots=None, max_cycles=args.plain_cycles)
+        e1.record(stream)
+        e1.synchronize()
+        plain = {"ms": round(e0.elapsed_time(e1), 3), "iters": sp["iters"],
+                 "cycles": sp["cycles"], "converged": bool(sp["converged"]),
+                 "true_relres": sp["true_relres"], "cycle_cap": args.plain_cycles}
+
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": P.A.n, "nnz": P.A.nnz, "d": P.d,
+                   "degree_with_added": st_degree(stats, R), "m": P.m, "tol": P.tol,
+                   "l2": "flushed (512 MB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "iters": st["iters"], "cycles": st["cycles"], "mvps": st["mvps"], "dots": st["dots"],
+        "true_relres": rel, "converged": bool(st["converged"]),
+        "roofline": {"bound": "hbm", "kernel": "k_spmv_step (fused SpMV-root, Alg 1/3)",
+                     "achieved": round(achieved, 1) if achieved else None,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4) if achieved else None,
+                     "traffic": traffic, "launches": poly_launches,
+                     "bytes_per_launch": round(poly_bytes / max(poly_launches, 1))},
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "plain_gmres50": plain,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        s = _run_oracle_subprocess(args.oracle_iters)
+        v = _extrapolate(s, st["iters"], st["cycles"])
+        line["cpu_baseline"] = {
+            "value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle build_poly(d=40) + %d PP-GMRES(50) iterations + one restart "
+                      "update on this workload, extrapolated to this run's %d iterations / "
+                      "%d restarts (oracle build %.2f s, %.3f s/iteration)"
+                      % (s["n_iters"], st["iters"], st["cycles"], s["t_build"], s["t_iter"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def st_degree(stats, R):
+    return int(R.n_total)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-cycles", type=int, default=400)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-iters", type=int, default=2)
+    ap.add_argument("--ref-iters", type=int, default=200)
+    ap.add_argument("--ref-cycles", type=int, default=4)
+    ap.add_argument("--oracle-sample", type=int, default=None)
+    args = ap.parse_args()
+    if args.oracle_sample is not None:
+        print(json.dumps(oracle_sample(args.oracle_sample)))
+        return 0
+    rank, local, world = _dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, local, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+/*
+ * ppgmres.h -- C ABI of libppgmres, a GB300 (sm_103a) implementation of
+ * polynomial-preconditioned GMRES with the GMRES polynomial in root form
+ * (Loe & Morgan, "Toward Efficient Polynomial Preconditioning for GMRES").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Sparse matrices are CSR with int32 indices (ppg_csr).  Column indices
+ *    are sorted within a row and lie in [0, n).  All CSR arrays and all
+ *    vectors passed to device entry points are DEVICE pointers owned by the
+ *    caller; the library never frees them and never keeps them after the
+ *    call returns.
+ *  - Vectors have n entries of the CSR's dtype unless stated otherwise
+ *    (double for PPG_F64, float for PPG_F32).  Input and output vectors of
+ *    one call must not alias.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it.  Entry points that need a result on
+ *    the host (build_poly, solve, stability_check, csr_validate)
+ *    synchronise the stream before returning; apply_poly, apply_phi, spmv,
+ *    csr_transpose and adjoint_vals_grad are asynchronous.
+ *  - Scratch memory is taken stream-ordered (cudaMallocAsync) and returned
+ *    (cudaFreeAsync) before the call returns.
+ *  - Return codes: 0 = success, > 0 = soft status, < 0 = error (see
+ *    PPG_* below; ppg_strerror gives a message).  No C++ exception crosses
+ *    this interface.  After PPG_ERR_CUDA the CUDA error is also reported by
+ *    ppg_last_cuda_error().
+ *
+ * Host-only entry points (marked HOST) run on the CPU and need no GPU.
+ */
+#ifndef PPGMRES_H
+#define PPGMRES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPG_ABI_VERSION 1
+
+/* status codes */
+#define PPG_OK                0
+#define PPG_NOT_CONVERGED     1   /* max_cycles reached; x holds the last iterate */
+#define PPG_LUCKY_BREAKDOWN   2   /* build_poly: Krylov space invariant before d steps */
+#define PPG_ERR_ARG          -1   /* bad argument (NULL, size, aliasing, dtype) */
+#define PPG_ERR_CSR          -2   /* CSR structure invalid */
+#define PPG_ERR_SINGULAR_H   -3   /* H_dd singular: harmonic Ritz values undefined */
+#define PPG_ERR_NONFINITE    -4   /* NaN or Inf met in a residual or in H */
+#define PPG_ERR_CUDA         -5   /* a CUDA runtime call failed */
+#define PPG_ERR_CAPACITY     -6   /* ppg_roots arrays too small; n_total = needed */
+#define PPG_ERR_EIG          -7   /* Hessenberg QR did not converge */
+#define PPG_ERR_NOMEM        -8   /* device scratch allocation failed */
+
+/* dtypes */
+#define PPG_F64 0
+#define PPG_F32 1
+
+/* CSR matrix (Algorithms 1 and 3 take "sparse matrix A"): device pointers. */
+typedef struct ppg_csr {
+    int32_t n;              /* rows = columns */
+    int32_t nnz;
+    const int32_t* rowptr;  /* [n+1], rowptr[0] = 0, rowptr[n] = nnz */
+    const int32_t* colind;  /* [nnz] */
+    const void* vals;       /* [nnz] double (PPG_F64) or float (PPG_F32) */
+    int32_t dtype;
+} ppg_csr;
+
+/* Roots of the GMRES residual polynomial pi (eq 2.1), Leja-ordered, with
+ * the copies added by the stability control of Algorithm 2.  HOST arrays
+ * owned by the caller, each of `capacity` entries.  Conjugate pairs are
+ * adjacent, +Im member first, and are exact conjugates; a root is real iff
+ * im == 0.  log10_pof (may be NULL) receives log10 pof(k) of the n_orig
+ * original roots in Leja order. */
+typedef struct ppg_roots {
+    int32_t n_orig;     /* original degree d actually reached */
+    int32_t n_added;    /* roots added by Algorithm 2 */
+    int32_t n_total;    /* n_orig + n_added = degree of pi and phi */
+    int32_t capacity;   /* entries available in re/im */
+    double* re;
+    double* im;
+    double* log10_pof;  /* optional, n_orig entries */
+} ppg_roots;
+
+typedef struct ppg_opts {
+    int32_t max_cycles;            /* restart cap (default 10000) */
+    int32_t stability_control;     /* 1: add roots by Algorithm 2 (default 1) */
+    double  pof_threshold_log10;   /* default 4  (pof > 1e4 adds a root) */
+    double  pof_step_log10;        /* default 14 (one more per factor 1e14) */
+    int32_t timing;                /* 1: record CUDA-event times into stats */
+    int32_t x0_given;              /* 1: x holds the initial guess (default 0: x0 = 0) */
+} ppg_opts;
+
+typedef struct ppg_stats {
+    int64_t iters;          /* Arnoldi steps of the outer (F)GMRES */
+    int64_t cycles;         /* restarts + 1 */
+    int64_t mvps;           /* every SpMV: d per phi(A)v, d-1 per p(A)v, 1 per residual */
+    int64_t dots;           /* dot products and norms of length n */
+    int64_t launches;       /* kernels this call launched */
+    double  true_relres;    /* ||b - A x|| / ||b|| at return */
+    double  est_relres;     /* last shortcut residual |g_{j+1}| / ||b|| */
+    int32_t converged;
+    int32_t pad_;
+    /* filled when opts.timing = 1: the fused SpMV-root kernels of the
+     * polynomial chains (Algorithms 1 and 3) */
+    double  poly_ms;        /* summed CUDA-event time of those launches */
+    int64_t poly_launches;
+    double  poly_bytes;     /* algorithmic bytes of those launches */
+    double  ortho_ms;       /* CGS2 + Givens kernels */
+} ppg_stats;
+
+/* ---- library ---------------------------------------------------------- */
+
+int32_t     ppg_abi_version(void);
+const char* ppg_strerror(int32_t code);
+const char* ppg_last_cuda_error(void);
+void        ppg_default_opts(ppg_opts* opts);
+/* Kernels launched so far by the calling host thread (all entry points). */
+int64_t     ppg_launch_count(void);
+
+/* ---- HOST: polynomial construction steps (Algorithm 4 step 1(b)-(c)) ---- */
+
+/* Harmonic Ritz values theta_1..theta_d (Algorithm 4 step 1(b)): the
+ * eigenvalues of H_dd + h_{d+1,d}^2 f e_d^T with H_dd^T f = e_d.  Hbar is
+ * the (d+1) x d upper Hessenberg matrix of the Arnoldi relation
+ * A V_d = V_{d+1} Hbar, column-major with leading dimension ldh >= d+1.
+ * re/im receive d values (unordered).  HOST.  Errors: PPG_ERR_ARG,
+ * PPG_ERR_SINGULAR_H, PPG_ERR_EIG, PPG_ERR_NONFINITE. */
+int32_t ppg_harmonic_ritz(const double* Hbar, int32_t ldh, int32_t d,
+                          double* re, double* im);
+
+/* Modified Leja ordering (Section 2; Algorithm 2 step 1) of k roots closed
+ * under conjugation: largest modulus first, then each next root maximises
+ * the sum of log-distances to those chosen; a non-real root is followed by
+ * its conjugate (+Im first); ties go to the larger real part, then the
+ * larger imaginary part.  HOST.  Errors: PPG_ERR_ARG (not conjugation
+ * closed). */
+int32_t ppg_leja_order(int32_t k, const double* re, const double* im,
+                       double* re_out, double* im_out);
+
+/* Algorithm 2 steps 2-3 on k Leja-ordered roots: pof(k) =
+ * prod_{i != k} |1 - theta_k/theta_i|; ceil((log10 pof - thr)/step) copies
+ * when positive; the first copy is appended, further copies spread evenly
+ * between the root and the end of the list (pairs kept together).  Writes
+ * out->re/im/n_*.  HOST.  Errors: PPG_ERR_ARG, PPG_ERR_CAPACITY. */
+int32_t ppg_add_roots(int32_t k, const double* re, const double* im,
+                      double thr_log10, double step_log10, ppg_roots* out);
+
+/* Steps 1(b) and 1(c) together: harmonic Ritz values of Hbar, Leja order,
+ * and (if opts->stability_control) root adding.  HOST. */
+int32_t ppg_roots_from_hessenberg(const double* Hbar, int32_t ldh, int32_t d,
+                                  const ppg_opts* opts, ppg_roots* out);
+
+/* HOST: check CSR structure held in host memory (rowptr monotone from 0 to
+ * nnz, colind sorted within rows and in range).  Returns PPG_OK or
+ * PPG_ERR_CSR. */
+int32_t ppg_csr_validate_host(int32_t n, int32_t nnz, const int32_t* rowptr,
+                              const int32_t* colind);
+
+/* ---- DEVICE entry points ---------------------------------------------- */
+
+/* Algorithm 4 step 1: one cycle of GMRES(d) (d Arnoldi steps, CGS2) from
+ * the device vector v0 (FP64, need not be normalised), then harmonic Ritz
+ * values, Leja order and root adding on the host in FP64.  A must be
+ * PPG_F64.  Hbar_host (nullable) receives the (d+1) x d Hessenberg matrix,
+ * column-major, ld = d+1.  Returns PPG_LUCKY_BREAKDOWN (with
+ * out->n_orig < d) if h_{j+1,j} <= 1e-13 ||A v_j|| at some step.
+ * Synchronises `stream`. */
+int32_t ppg_build_poly(const ppg_csr* A, int32_t d, const double* v0,
+                       const ppg_opts* opts, ppg_roots* out, double* Hbar_host,
+                       void* stream);
+
+/* y = p(A) v by Algorithm 3: d-1 fused SpMV-root passes (two per conjugate
+ * pair, the last pair's second one omitted), vectors in A's dtype.  For
+ * PPG_F32 the root coefficients 1/theta, 2a and 1/(a^2+b^2) are rounded to
+ * float.  Asynchronous. */
+int32_t ppg_apply_poly(const ppg_csr* A, const ppg_roots* r, const void* v,
+                       void* y, void* stream);
+
+/* y = phi(A) v = v - pi(A) v by Algorithm 1: d fused SpMV-root passes.
+ * Asynchronous. */
+int32_t ppg_apply_phi(const ppg_csr* A, const ppg_roots* r, const void* v,
+                      void* y, void* stream);
+
+/* y = A x.  Asynchronous. */
+int32_t ppg_spmv(const ppg_csr* A, const void* x, void* y, void* stream);
+
+/* Algorithm 4 step 2: restarted GMRES(m) on phi(A) y = b with phi applied
+ * by Algorithm 1, and x = p(A) y by Algorithm 3 at each restart; the next
+ * cycle starts from the true residual b - A x.  r == NULL or
+ * r->n_total == 0 runs plain GMRES(m) on A.  CGS2 orthogonalisation,
+ * Givens least squares; a cycle ends at m steps or when the shortcut
+ * residual |g_{j+1}| <= tol ||b||; the solve converges when the true
+ * residual ||b - A x|| <= tol ||b||.  A PPG_F64; b, x device double.
+ * Returns PPG_OK, PPG_NOT_CONVERGED or an error.  Synchronises. */
+int32_t ppg_solve(const ppg_csr* A, const ppg_roots* r, const double* b,
+                  double* x, int32_t m, double tol, const ppg_opts* opts,
+                  ppg_stats* stats, void* stream);
+
+/* Precision form: flexible GMRES(m) in FP64 with the right preconditioner
+ * z_j = p(A) v_j computed by Algorithm 3 in FP32 on A32 (the same matrix
+ * with float values; rowptr/colind may be shared with A64).  The Arnoldi
+ * orthogonalisation, Givens least squares, w = A64 z_j and the true
+ * residual are FP64.  x = x0 + Z y.  Synchronises. */
+int32_t ppg_solve_flex(const ppg_csr* A64, const ppg_csr* A32,
+                       const ppg_roots* r, const double* b, double* x,
+                       int32_t m, double tol, const ppg_opts* opts,
+                       ppg_stats* stats, void* stream);
+
+/* Stability check StCh of Section 3.5: ||r1 - r2|| with r1 = b - A p(A) b
+ * (Algorithm 3) and r2 = pi(A) b = b - phi(A) b (Algorithm 1).  A PPG_F64,
+ * b device double.  Writes the host double *stch.  Synchronises. */
+int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r,
+                            const double* b, double* stch, void* stream);
+
+/* Transposed CSR of A (for the adjoint solve with A^T): rowptr_t [n+1],
+ * colind_t [nnz], vals_t [nnz] in A's dtype, all device, caller-owned.
+ * perm (nullable, [nnz]) receives for each entry of A^T the index of the
+ * same entry in A.  Columns of A^T come out sorted.  Asynchronous. */
+int32_t ppg_csr_transpose(const ppg_csr* A, int32_t* rowptr_t,
+                          int32_t* colind_t, void* vals_t, int32_t* perm,
+                          void* stream);
+
+/* Adjoint gradient on the sparsity pattern: for x solving A x = b and
+ * lambda solving A^T lambda = dL/dx, dL/dvals[k] = -lambda[row(k)] *
+ * x[colind[k]] (dL/db = lambda needs no kernel).  FP64.  Asynchronous. */
+int32_t ppg_adjoint_vals_grad(const ppg_csr* A, const double* lambda,
+                              const double* x, double* gvals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPGMRES_H */

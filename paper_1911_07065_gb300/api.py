@@ -1,0 +1,228 @@
+"""PyTorch-facing API over the C ABI (argument marshalling only).
+
+Device vectors are torch tensors on a CUDA device; every computation is a
+call into libppgmres on the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from ._binding import (PPG_F32, PPG_F64, PPGError, Roots, check, default_opts, lib,
+                       ppg_csr, ppg_stats, csr_validate_host, _dp)
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected contiguous CUDA tensors")
+
+
+class CSR:
+    """CSR matrix on the device: int32 rowptr/colind, float64 or float32 vals."""
+
+    def __init__(self, rowptr: torch.Tensor, colind: torch.Tensor, vals: torch.Tensor):
+        _need_cuda(rowptr, colind, vals)
+        if rowptr.dtype != torch.int32 or colind.dtype != torch.int32:
+            raise ValueError("rowptr/colind must be int32")
+        if vals.dtype not in (torch.float64, torch.float32):
+            raise ValueError("vals must be float64 or float32")
+        self.rowptr, self.colind, self.vals = rowptr, colind, vals
+        self.n = rowptr.numel() - 1
+        self.nnz = colind.numel()
+        self.s = ppg_csr(self.n, self.nnz, rowptr.data_ptr(), colind.data_ptr(),
+                         vals.data_ptr(), PPG_F64 if vals.dtype == torch.float64 else PPG_F32)
+
+    @property
+    def dtype(self):
+        return self.vals.dtype
+
+    @classmethod
+    def from_host(cls, rowptr, colind, vals, device="cuda", dtype=torch.float64,
+                  validate=True) -> "CSR":
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        colind = np.ascontiguousarray(colind, dtype=np.int32)
+        if validate:
+            rc = csr_validate_host(rowptr, colind)
+            check(rc, "ppg_csr_validate_host")
+        return cls(torch.from_numpy(rowptr).to(device), torch.from_numpy(colind).to(device),
+                   torch.from_numpy(np.asarray(vals)).to(device=device, dtype=dtype))
+
+    def with_vals(self, vals: torch.Tensor) -> "CSR":
+        return CSR(self.rowptr, self.colind, vals)
+
+    def astype(self, dtype) -> "CSR":
+        return CSR(self.rowptr, self.colind, self.vals.to(dtype))
+
+    def ref(self):
+        return C.byref(self.s)
+
+    def transpose(self, with_perm: bool = False, stream=None):
+        rp = torch.empty(self.n + 1, dtype=torch.int32, device=self.vals.device)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=self.vals.device)
+        vv = torch.empty(self.nnz, dtype=self.vals.dtype, device=self.vals.device)
+        perm = torch.empty(self.nnz, dtype=torch.int32, device=self.vals.device) if with_perm else None
+        check(lib.ppg_csr_transpose(self.ref(), _ptr(rp), _ptr(ci), _ptr(vv),
+                                    _ptr(perm) if perm is not None else None, _stream(stream)),
+              "ppg_csr_transpose")
+        T = CSR(rp, ci, vv)
+        return (T, perm) if with_perm else T
+
+
+def build_poly(A: CSR, d: int, v0: torch.Tensor, stability_control: bool = True,
+               return_hbar: bool = False, capacity: Optional[int] = None, stream=None):
+    """Algorithm 4 step 1 on the device; returns Roots (and Hbar)."""
+    _need_cuda(v0)
+    if v0.dtype != torch.float64:
+        raise ValueError("v0 must be float64")
+    cap = capacity or max(16, 4 * d)
+    r = Roots(cap)
+    H = np.zeros((d + 1) * d)
+    o = default_opts(stability_control=int(bool(stability_control)))
+    rc = lib.ppg_build_poly(A.ref(), d, _ptr(v0), C.byref(o), r.ref(), _dp(H), _stream(stream))
+    if rc == -6 and capacity is None:
+        return build_poly(A, d, v0, stability_control, return_hbar, r.s.n_total + 8, stream)
+    check(rc, "ppg_build_poly")
+    Hbar = H.reshape(d, d + 1).T.copy()
+    return (r, Hbar) if return_hbar else r
+
+
+def apply_poly(A: CSR, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+               stream=None) -> torch.Tensor:
+    """y = p(A) v (Algorithm 3) in A's dtype."""
+    _need_cuda(v)
+    y = torch.empty_like(v) if out is None else out
+    check(lib.ppg_apply_poly(A.ref(), roots.ref(), _ptr(v), _ptr(y), _stream(stream)),
+          "ppg_apply_poly")
+    return y
+
+
+def apply_phi(A: CSR, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+              stream=None) -> torch.Tensor:
+    """y = phi(A) v (Algorithm 1) in A's dtype."""
+    _need_cuda(v)
+    y = torch.empty_like(v) if out is None else out
+    check(lib.ppg_apply_phi(A.ref(), roots.ref(), _ptr(v), _ptr(y), _stream(stream)),
+          "ppg_apply_phi")
+    return y
+
+
+def spmv(A: CSR, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None):
+    _need_cuda(x)
+    y = torch.empty_like(x) if out is None else out
+    check(lib.ppg_spmv(A.ref(), _ptr(x), _ptr(y), _stream(stream)), "ppg_spmv")
+    return y
+
+
+def solve(A: CSR, b: torch.Tensor, m: int = 50, tol: float = 1e-10,
+          roots: Optional[Roots] = None, x0: Optional[torch.Tensor] = None,
+          max_cycles: int = 10000, timing: bool = False, out: Optional[torch.Tensor] = None,
+          stream=None) -> Tuple[torch.Tensor, dict]:
+    """PP-GMRES(m) (roots given) or GMRES(m); returns (x, stats)."""
+    _need_cuda(b)
+    x = torch.empty_like(b) if out is None else out
+    if x0 is not None:
+        x.copy_(x0)
+    o = default_opts(max_cycles=max_cycles, timing=int(timing), x0_given=int(x0 is not None))
+    st = ppg_stats()
+    rc = lib.ppg_solve(A.ref(), roots.ref() if roots is not None else None, _ptr(b), _ptr(x),
+                       m, tol, C.byref(o), C.byref(st), _stream(stream))
+    check(rc, "ppg_solve")
+    s = st.as_dict()
+    s["status"] = rc
+    return x, s
+
+
+def solve_flex(A64: CSR, A32: CSR, b: torch.Tensor, roots: Roots, m: int = 50,
+               tol: float = 1e-10, max_cycles: int = 10000, timing: bool = False,
+               out: Optional[torch.Tensor] = None, stream=None):
+    """FGMRES(m) in FP64 with p(A) applied in FP32 on A32; returns (x, stats)."""
+    _need_cuda(b)
+    x = torch.empty_like(b) if out is None else out
+    o = default_opts(max_cycles=max_cycles, timing=int(timing))
+    st = ppg_stats()
+    rc = lib.ppg_solve_flex(A64.ref(), A32.ref(), roots.ref(), _ptr(b), _ptr(x), m, tol,
+                            C.byref(o), C.byref(st), _stream(stream))
+    check(rc, "ppg_solve_flex")
+    s = st.as_dict()
+    s["status"] = rc
+    return x, s
+
+
+def stability_check(A: CSR, roots: Roots, b: torch.Tensor, stream=None) -> float:
+    """StCh = ||(b - A p(A) b) - pi(A) b|| (Section 3.5)."""
+    _need_cuda(b)
+    out = C.c_double(0.0)
+    check(lib.ppg_stability_check(A.ref(), roots.ref(), _ptr(b), C.byref(out), _stream(stream)),
+          "ppg_stability_check")
+    return out.value
+
+
+def adjoint_vals_grad(A: CSR, lam: torch.Tensor, x: torch.Tensor, out=None, stream=None):
+    g = torch.empty_like(A.vals) if out is None else out
+    check(lib.ppg_adjoint_vals_grad(A.ref(), _ptr(lam), _ptr(x), _ptr(g), _stream(stream)),
+          "ppg_adjoint_vals_grad")
+    return g
+
+
+def solve_host(rowptr: np.ndarray, colind: np.ndarray, vals: np.ndarray, b: np.ndarray,
+               v0: np.ndarray, d: int, m: int = 50, tol: float = 1e-10,
+               device="cuda", timing: bool = False):
+    """End-to-end call from host arrays: copy CSR, b and v0 to the device,
+    build the polynomial, solve, copy x back.  Returns (x, roots, stats)."""
+    def pinned(a, dt):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+        return t.pin_memory()
+    rp = pinned(rowptr, np.int32).to(device, non_blocking=True)
+    ci = pinned(colind, np.int32).to(device, non_blocking=True)
+    vv = pinned(vals, np.float64).to(device, non_blocking=True)
+    bd = pinned(b, np.float64).to(device, non_blocking=True)
+    vd = pinned(v0, np.float64).to(device, non_blocking=True)
+    A = CSR(rp, ci, vv)
+    roots = build_poly(A, d, vd)
+    x, st = solve(A, bd, m, tol, roots=roots, timing=timing)
+    xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    xh.copy_(x, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return xh.numpy(), roots, st
+
+
+class PPGMRESFunction(torch.autograd.Function):
+    """x = A(vals)^{-1} b by PP-GMRES, differentiable in b and vals.
+
+    Backward runs the adjoint PP-GMRES on A^T with the same roots
+    (p(A^T) = p(A)^T): lambda = A^{-T} grad_x, dL/db = lambda and
+    dL/dvals[k] = -lambda[row k] x[colind k].
+    """
+
+    @staticmethod
+    def forward(ctx, b, vals, A: CSR, roots: Roots, m: int, tol: float, AT: Optional[CSR]):
+        Aw = A.with_vals(vals.detach().contiguous())
+        x, st = solve(Aw, b.detach().contiguous(), m, tol, roots=roots)
+        ctx.A, ctx.roots, ctx.m, ctx.tol, ctx.AT = Aw, roots, m, tol, AT
+        ctx.save_for_backward(x)
+        ctx.stats = st
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        AT = ctx.AT
+        if AT is None:
+            AT = ctx.A.transpose()
+        lam, _ = solve(AT, gx.contiguous(), ctx.m, ctx.tol, roots=ctx.roots)
+        gvals = adjoint_vals_grad(ctx.A, lam, x)
+        return lam, gvals, None, None, None, None, None

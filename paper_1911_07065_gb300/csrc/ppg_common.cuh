@@ -1,0 +1,193 @@
+// Internal declarations shared by the libppgmres translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "../../include/ppgmres.h"
+
+namespace ppg {
+
+// ---------------------------------------------------------------------------
+// Errors and bookkeeping
+// ---------------------------------------------------------------------------
+
+void set_cuda_error(cudaError_t e, const char* where);
+extern thread_local int64_t g_launches;   // kernels launched by this thread
+
+#define PPG_CUDA(call)                                                    \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) {                                          \
+            ::ppg::set_cuda_error(e_, #call);                             \
+            return PPG_ERR_CUDA;                                          \
+        }                                                                 \
+    } while (0)
+
+#define PPG_TRY(expr)                                                     \
+    do {                                                                  \
+        int32_t rc_ = (expr);                                             \
+        if (rc_ < 0) return rc_;                                          \
+    } while (0)
+
+int32_t check_launch(const char* where);
+
+// ---------------------------------------------------------------------------
+// Fused SpMV-root step (one pass over A per root; Algorithms 1 and 3)
+// ---------------------------------------------------------------------------
+
+enum StepOp : int {
+    OP_SPMV = 0,      // o0 = A x
+    OP_RESID = 1,     // o0 = a0 - A x, part[block] = sum o0^2
+    OP_PHI_REAL = 2,  // pi' = a0 - c1 (A x)               (x = a0 = pi)
+    OP_PHI_PAIR2 = 3, // pi' = a1 + c2 (A x - c1 a0)       (x = a0 = prod, a1 = pi)
+    OP_P_REAL = 4,    // p' = a1 + c1 a0 ; prod' = a0 - c1 (A x)   (x = a0 = prod)
+    OP_P_PAIR1 = 5,   // tmp = c1 a0 - A x ; p' = a1 + c2 tmp      (x = a0 = prod)
+    OP_P_PAIR2 = 6,   // prod' = a0 - c2 (A x)                     (x = tmp, a0 = prod)
+};
+
+enum StepFlag : int {
+    F_FINAL = 1,   // PHI_*: o0 = a2 - pi' ; P_REAL: o0 = p' + c3 prod' ;
+                   // P_PAIR2: o0 = a1 + c3 prod'
+    F_PZERO = 2,   // P_*: the accumulator p starts at zero (a1 not read)
+    F_NO_O1 = 4,   // P_PAIR1: tmp not needed afterwards
+};
+
+template <typename T>
+struct StepArgs {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const T* vals;
+    int32_t n;
+    const T* x;
+    const T* a0;
+    const T* a1;
+    const T* a2;
+    T* o0;
+    T* o1;
+    T c1, c2, c3;
+    int32_t flags;
+    double* part;
+};
+
+// launch one fused step; returns the number of blocks (= partial sums for
+// OP_RESID) or a negative status
+template <typename T>
+int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s);
+
+int32_t spmv_grid_blocks(int32_t n);
+
+// algorithmic bytes of one fused step
+double step_bytes(int op, int flags, int64_t n, int64_t nnz, int elem);
+
+// ---------------------------------------------------------------------------
+// Root-step plans (host side; built once per roots and reused)
+// ---------------------------------------------------------------------------
+
+enum BufId : int { B_IN = 0, B_OUT = 1, B_A = 2, B_B = 3, B_C = 4, B_P = 5, B_NONE = -1 };
+
+struct Step {
+    int op;
+    int flags;
+    double c1, c2, c3;
+    int x, a0, a1, a2, o0, o1;   // BufId
+};
+
+// Algorithm 1: in = v, out = phi(A) v (or pi(A) v when want_pi)
+std::vector<Step> plan_phi(const double* re, const double* im, int d, bool want_pi);
+// Algorithm 3: in = v; accumulator B_P (starts at zero unless accumulate)
+std::vector<Step> plan_p(const double* re, const double* im, int d, bool accumulate);
+
+struct Buffers {
+    void* ptr[6];
+};
+
+template <typename T>
+int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr,
+                 const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
+                 const Buffers& bufs, cudaStream_t s, double* bytes_out);
+
+// ---------------------------------------------------------------------------
+// Orthogonalisation and small dense kernels
+// ---------------------------------------------------------------------------
+
+struct OrthoWs {
+    double* part;       // [grid * (MAXC + 2)]
+    unsigned* counter;  // [4] zero-initialised, self-resetting
+    double* h1;         // [MAXC + 2]
+    double* h2;         // [MAXC + 2]
+    double* nrm;        // [4]
+    int grid;
+};
+
+constexpr int ORTHO_MAXC = 256;   // max columns (m + 1)
+
+int ortho_grid(int32_t n);
+size_t ortho_part_doubles(int grid);
+
+// h_out = V[:, :ncol]^T w  (+ w.w in h_out[ncol] if with_self)
+int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w,
+                       int32_t n, bool with_self, double* h_out,
+                       const OrthoWs& ws, cudaStream_t s);
+// w -= V hin ; then h_out = V^T w (mode 1) or h_out[0] = w.w (mode 2)
+int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w,
+                          int32_t n, const double* hin, int mode, double* h_out,
+                          const OrthoWs& ws, cudaStream_t s);
+
+struct GmresState {   // device, one per solve
+    double* R;        // (m+1) x m column-major, rotated Hessenberg
+    double* Hraw;     // (m+1) x m column-major, un-rotated (build_poly)
+    double* cs;       // [m]
+    double* sn;       // [m]
+    double* g;        // [m+1]
+    double* y;        // [m]
+    double* scal;     // [8]: 0 est, 1 h_{j+1,j}, 2 inv_h, 3 beta, 4 inv_beta,
+                      //      5 breakdown flag, 6 first breakdown step, 7 spare
+};
+
+// Hessenberg column j from h1 + h2 and nrm (w.w); givens = apply rotations
+// and update g; breakdown_rtol > 0 compares h_{j+1,j} with
+// breakdown_rtol * sqrt(w0sq) where w0sq = h1[ncol]
+int32_t launch_finish_column(const GmresState& st, int ldh, int j,
+                             const double* h1, const double* h2,
+                             const double* nrm, bool givens, double bnorm,
+                             double breakdown_rtol, cudaStream_t s);
+int32_t launch_scale(const double* x, double* y, int32_t n, const double* scal_ptr,
+                     cudaStream_t s);
+int32_t launch_backsolve(const GmresState& st, int ldh, int k, cudaStream_t s);
+template <typename TV>
+int32_t launch_gemv_acc(const TV* V, int64_t ldv, int k, const double* y,
+                        double* out, int32_t n, bool accumulate, cudaStream_t s);
+int32_t launch_reduce_norm(const double* part, int nparts, double* scal,
+                           double* g0, cudaStream_t s);
+int32_t launch_norm2_part(const double* x, int32_t n, double* part,
+                          cudaStream_t s, int* nparts);
+int32_t launch_diff_norm2_part(const double* a, const double* b, int32_t n,
+                               double* part, cudaStream_t s, int* nparts);
+int32_t launch_cast_f64_f32(const double* x, float* y, int32_t n, cudaStream_t s);
+int32_t launch_cast_f32_f64(const float* x, double* y, int32_t n, cudaStream_t s);
+int32_t launch_fill(double* x, double v, int32_t n, cudaStream_t s);
+template <typename T>
+int32_t launch_axpby(T a, const T* x, T b, const T* y, T* out, int32_t n,
+                     cudaStream_t s);
+
+// transpose / adjoint
+int32_t launch_transpose(const ppg_csr* A, int32_t* rowptr_t, int32_t* colind_t,
+                         void* vals_t, int32_t* perm, int32_t* work,
+                         cudaStream_t s);
+int32_t launch_adjoint_grad(const ppg_csr* A, const double* lam,
+                            const double* x, double* gvals, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Host polynomial construction (host_poly.cpp)
+// ---------------------------------------------------------------------------
+
+int32_t host_harmonic_ritz(const double* Hbar, int ldh, int d, double* re, double* im);
+int32_t host_leja(int k, const double* re, const double* im, double* ro, double* io);
+int32_t host_add_roots(int k, const double* re, const double* im, double thr,
+                       double step, ppg_roots* out);
+
+}  // namespace ppg

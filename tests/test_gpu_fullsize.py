@@ -1,0 +1,125 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (run with -m gpu).
+
+* 2-D convection-diffusion 1000 x 1000 (n = 1e6): p(A) v against the oracle
+  on seeded vectors with the oracle's own roots, the device-built roots
+  against the oracle's, and the full PP-GMRES solve checked by its true
+  residual computed on the host.
+* 3-D convection-diffusion 160^3 (n = 4.1e6): FP32 p(A) v against the
+  oracle's float32 Algorithm 3, and the FP32-inner flexible solve checked by
+  its true residual.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gmres, poly
+
+from gpu_util import dev_csr, ppg_or_skip, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    return ppg_or_skip()
+
+
+@pytest.fixture(scope="module")
+def cd2d(env):
+    p, torch = env
+    P = synth.problem("cd2d_1000")
+    As = P.A.to_scipy()
+    orc = poly.build_poly(As, P.d, P.v0)
+    return P, As, orc, dev_csr(p, torch, P.A)
+
+
+def _pnorm_lower(As, roots, n, iters=3):
+    """A lower bound of ||p(A)||_2 (a few power steps): using it as the
+    error scale makes the check stricter, not looser."""
+    ATs = As.T.tocsr()
+    v = np.random.default_rng(0).standard_normal(n)
+    v /= np.linalg.norm(v)
+    est = 0.0
+    for _ in range(iters):
+        w = poly.apply_p(As, roots, v)
+        est = np.linalg.norm(w)
+        v = poly.apply_p(ATs, roots, w)
+        v /= np.linalg.norm(v)
+    return est
+
+
+def test_cd2d_1000_apply_p_and_phi(env, cd2d):
+    p, torch = env
+    P, As, orc, Ad = cd2d
+    R = p.Roots.from_complex(orc.roots)
+    pn = _pnorm_lower(As, orc.roots, P.A.n)
+    for seed in (1, 2):
+        v = np.random.default_rng(seed).standard_normal(P.A.n)
+        y = p.apply_poly(Ad, R, to_dev(torch, v)).cpu().numpy()
+        ref = poly.apply_p(As, orc.roots, v)
+        scale = pn * np.linalg.norm(v)
+        assert np.linalg.norm(y - ref) <= 1e-11 * scale
+        assert np.max(np.abs(y - ref)) <= 1e-11 * scale
+    v = np.random.default_rng(3).standard_normal(P.A.n)
+    y = p.apply_phi(Ad, R, to_dev(torch, v)).cpu().numpy()
+    ref = poly.apply_phi(As, orc.roots, v)
+    assert np.linalg.norm(y - ref) <= 1e-11 * np.linalg.norm(v) * max(1.0, np.linalg.norm(ref) / np.linalg.norm(v))
+
+
+def test_cd2d_1000_roots_and_solve(env, cd2d):
+    p, torch = env
+    P, As, orc, Ad = cd2d
+    R = p.build_poly(Ad, P.d, to_dev(torch, P.v0))
+    assert R.n_total == orc.roots.size
+    # eigenvalue condition numbers of the harmonic-Ritz matrix (oracle side)
+    import scipy.linalg as sla
+    H = orc.Hbar
+    d = H.shape[1]
+    e = np.zeros(d); e[-1] = 1
+    f = np.linalg.solve(H[:d, :d].T, e)
+    G = H[:d, :d].copy(); G[:, -1] += H[d, d - 1] ** 2 * f
+    w, vl, vr = sla.eig(G, left=True, right=True)
+    kappa = 1.0 / np.abs(np.sum(vl.conj() * vr, axis=0))
+    for t in R.complex():
+        i = int(np.argmin(np.abs(w - t)))
+        assert abs(w[i] - t) / abs(w[i]) <= 1e-10 * max(1.0, kappa[i])
+    x, st = p.solve(Ad, to_dev(torch, P.b), P.m, P.tol, roots=R)
+    rel = np.linalg.norm(P.b - As @ x.cpu().numpy()) / np.linalg.norm(P.b)
+    assert st["converged"] == 1 and rel <= P.tol
+
+
+@pytest.fixture(scope="module")
+def cd3d(env):
+    p, torch = env
+    P = synth.problem("cd3d_160")
+    small = synth.problem("cd3d_160", scale=40)
+    orc = poly.build_poly(small.A.to_scipy(), 60, small.v0)
+    return P, orc.roots
+
+
+def test_cd3d_160_fp32_apply_p(env, cd3d):
+    p, torch = env
+    P, roots = cd3d
+    A32 = dev_csr(p, torch, P.A, dtype=torch.float32)
+    As32 = P.A.to_scipy().astype(np.float32)
+    v = np.random.default_rng(4).standard_normal(P.A.n).astype(np.float32)
+    y = p.apply_poly(A32, p.Roots.from_complex(roots), to_dev(torch, v, torch.float32))
+    y = y.cpu().numpy().astype(np.float64)
+    ref = gmres.apply_p32(As32, gmres._roots32(roots), v).astype(np.float64)
+    # scale: the FP64 result's norm bounds ||p(A)|| ||v|| from below
+    ref64 = poly.apply_p(P.A.to_scipy(), roots, v.astype(np.float64))
+    scale = np.linalg.norm(ref64)
+    assert np.linalg.norm(y - ref) <= 2e-5 * scale
+    assert np.linalg.norm(y - ref64) <= 1e-3 * scale
+
+
+def test_cd3d_160_flex_solve(env, cd3d):
+    p, torch = env
+    P, _ = cd3d
+    A64 = dev_csr(p, torch, P.A)
+    A32 = A64.astype(torch.float32)
+    R = p.build_poly(A64, P.d, to_dev(torch, P.v0))
+    x, st = p.solve_flex(A64, A32, to_dev(torch, P.b), R, P.m, P.tol)
+    rel = np.linalg.norm(P.b - P.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(P.b)
+    assert st["converged"] == 1 and rel <= P.tol
