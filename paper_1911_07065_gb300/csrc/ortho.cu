@@ -56,11 +56,14 @@ __global__ void __launch_bounds__(ORTHO_THREADS)
 k_cgs(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
       const double* __restrict__ hin, int with_self, double* part, unsigned* counter,
       double* hout) {
+    // shared layout (doubles): sV [tilecols][ORTHO_TR] | sw [ORTHO_TR] |
+    // sh [ORTHO_MAXC] | sred [ORTHO_WARPS][ORTHO_TR]; MODE 0 stages no V tile
     extern __shared__ double smem[];
-    double* sV = smem;                                  // [ncol][ORTHO_TR]
-    double* sw = sV + (size_t)ncol * ORTHO_TR;          // [ORTHO_TR]
-    double* sh = sw + ORTHO_TR;                         // [ncol]
-    double* sred = sh + ORTHO_MAXC;                     // [ORTHO_WARPS][ORTHO_TR]
+    const int tilecols = (MODE == 0) ? 0 : ncol;
+    double* sV = smem;
+    double* sw = sV + (size_t)tilecols * ORTHO_TR;
+    double* sh = sw + ORTHO_TR;
+    double* sred = sh + ORTHO_MAXC;
     __shared__ bool am_last;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -149,8 +152,10 @@ k_cgs(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
     }
 }
 
-static size_t cgs_smem(int ncol) {
-    return sizeof(double) * ((size_t)ncol * ORTHO_TR + ORTHO_TR + ORTHO_MAXC +
+// dynamic shared bytes for a launch staging `tilecols` columns of V (the
+// kernel's layout above; MODE 0 passes 0)
+static size_t cgs_smem(int tilecols) {
+    return sizeof(double) * ((size_t)tilecols * ORTHO_TR + ORTHO_TR + ORTHO_MAXC +
                              ORTHO_WARPS * ORTHO_TR);
 }
 
