@@ -319,7 +319,9 @@ static int32_t run_solve(SolveCore& c) {
 
     if (pp) {
         c.phi_plan = plan_phi(c.roots->re, c.roots->im, d, false);
-        c.p_plan = plan_p(c.roots->re, c.roots->im, d, true);
+        // plain form: x += p(A) u accumulates into x; flexible form: z_j =
+        // p(A) v_j starts from zero
+        c.p_plan = plan_p(c.roots->re, c.roots->im, d, !c.flex);
     }
     Arena ar;
     c.ldv = pad_ld(n);

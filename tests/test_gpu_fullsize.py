@@ -6,7 +6,7 @@ benchmark times (run with -m gpu).
   against the oracle's, and the full PP-GMRES solve checked by its true
   residual computed on the host.
 * 3-D convection-diffusion 160^3 (n = 4.1e6): FP32 p(A) v against the
-  oracle's float32 Algorithm 3, and the FP32-inner flexible solve checked by
+  oracle's float32 Algorithm 3 (as accurate as it, both against FP64), and the FP32-inner flexible solve checked by
   its true residual.
 """
 import numpy as np
@@ -107,11 +107,15 @@ def test_cd3d_160_fp32_apply_p(env, cd3d):
     y = p.apply_poly(A32, p.Roots.from_complex(roots), to_dev(torch, v, torch.float32))
     y = y.cpu().numpy().astype(np.float64)
     ref = gmres.apply_p32(As32, gmres._roots32(roots), v).astype(np.float64)
-    # scale: the FP64 result's norm bounds ||p(A)|| ||v|| from below
+    # Two float32 runs of Algorithm 3 differ by rounding order only, so the
+    # device result must be about as accurate as the oracle's float32 run,
+    # both measured against the FP64 oracle.
     ref64 = poly.apply_p(P.A.to_scipy(), roots, v.astype(np.float64))
-    scale = np.linalg.norm(ref64)
-    assert np.linalg.norm(y - ref) <= 2e-5 * scale
-    assert np.linalg.norm(y - ref64) <= 1e-3 * scale
+    e_orc = np.linalg.norm(ref - ref64)
+    e_gpu = np.linalg.norm(y - ref64)
+    assert e_gpu <= 3.0 * e_orc
+    assert np.linalg.norm(y - ref) <= 4.0 * e_orc
+    assert e_gpu <= 1e-3 * np.linalg.norm(ref64)
 
 
 def test_cd3d_160_flex_solve(env, cd3d):

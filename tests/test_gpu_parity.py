@@ -4,8 +4,9 @@ Tolerances (FP64): SpMV within 1e-15 of the row's absolute sum; p(A) v and
 phi(A) v within 1e-11 ||p(A)||_2 ||v|| in norm and per element; Hbar within
 1e-10 relative; roots within 1e-10 max(1, kappa_i); solve: true residual
 <= tol and iteration count within 2 of the oracle.  FP32 (precision form):
-within 2e-5 ||p(A)||_2 ||v|| of the oracle's float32 Algorithm 3, a bound
-of about d * kappa * u32 for d <= 60 steps of unit-size updates.
+the device's float32 Algorithm 3 is as accurate as the oracle's float32 run
+(error against FP64 at most 3x the oracle's, difference at most 4x), and
+within 1e-5 ||p(A)||_2 ||v|| of it on the small cases.
 """
 import numpy as np
 import pytest
@@ -95,10 +96,14 @@ def test_apply_p_fp32_matches_float32_oracle(env, rname):
     y = p.apply_poly(Ad, R, to_dev(torch, v, torch.float32)).cpu().numpy().astype(np.float64)
     ref = gmres.apply_p32(As32, gmres._roots32(roots), v).astype(np.float64)
     As = A.to_scipy()
+    ref64 = poly.apply_p(As, roots, v.astype(np.float64))
+    e_orc = np.linalg.norm(ref - ref64)
+    assert np.linalg.norm(y - ref64) <= 3.0 * e_orc
+    assert np.linalg.norm(y - ref) <= 4.0 * e_orc
     pn = p_norm_estimate(lambda u: poly.apply_p(As, roots, u),
                          lambda u: poly.apply_p(As.T.tocsr(), roots, u), A.n)
     e2, einf = _scaled_err(y, ref, pn, v.astype(np.float64))
-    assert e2 <= 2e-5 and einf <= 2e-5
+    assert e2 <= 1e-5 and einf <= 1e-5
 
 
 def test_apply_on_matrix_with_long_and_empty_rows(env):
@@ -237,20 +242,31 @@ def test_solve_flex_fp32_inner_reaches_1e10(env):
 
 
 def test_stability_check_matches_oracle(env):
+    """StCh (Section 3.5) on a 20 x 20 convection-diffusion matrix with one
+    outlying diagonal entry: without root adding the degree-40 polynomial is
+    unstable (StCh huge on both sides), with it StCh is at rounding level.
+    StCh measures rounding, so only its magnitude class is compared.  (On a
+    diagonal matrix the fused multiply-add can cancel the outlier's
+    component exactly, which makes the unstable case look stable: a
+    non-diagonal matrix avoids that.)"""
     p, torch = env
-    lam = np.concatenate([np.linspace(1.0, 2.0, 400), [1e4]])
-    A = synth.diag_csr(lam)
+    A = synth.cd2d(20, 0.5)
+    k = A.rowptr[137] + 2
+    assert A.colind[k] == 137
+    A.vals[k] = 1e4
     As = A.to_scipy()
-    v0 = np.random.default_rng(1).standard_normal(401)
-    bb = np.random.default_rng(2).standard_normal(401)
+    v0 = np.random.default_rng(1).standard_normal(A.n)
+    bb = np.random.default_rng(2).standard_normal(A.n)
     bb /= np.linalg.norm(bb)
+    Ad = dev_csr(p, torch, A)
     for stab in (False, True):
         orc = poly.build_poly(As, 40, v0, stability=stab)
         s_orc = gmres.stability_check(As, orc.roots, bb)
-        s_gpu = p.stability_check(dev_csr(p, torch, A), p.Roots.from_complex(orc.roots),
-                                  to_dev(torch, bb))
-        # StCh measures rounding, so only its magnitude is comparable
-        assert s_gpu <= max(10 * s_orc, 1e-13) and s_gpu >= s_orc / 10 - 1e-13
+        s_gpu = p.stability_check(Ad, p.Roots.from_complex(orc.roots), to_dev(torch, bb))
+        if stab:
+            assert s_orc < 1e-10 and s_gpu < 1e-10
+        else:
+            assert s_orc > 1e-4 and s_gpu > 1e-4
 
 
 def test_transpose_and_adjoint_gradient(env):
