@@ -385,6 +385,39 @@ def st_degree(stats, R):
     return int(R.n_total)
 
 
+PROFILE_ROOTS = (7.5, 0.35, 3.9, 6.1, 1.6, 4.9)   # real roots spread over the spectrum
+
+
+def run_profile_case(name):
+    """A few launches of the fused SpMV-root kernel for an ncu capture:
+    ``phi_cd2d_2000``: Algorithm 1 on 2-D convection-diffusion 2000 x 2000
+    (n = 4e6, FP64; the matrix and vectors exceed L2), six real roots;
+    ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix."""
+    import numpy as np
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+    import synth
+
+    roots = ppg.Roots.from_complex(np.array(PROFILE_ROOTS, dtype=complex))
+    if name == "phi_cd2d_2000":
+        A = synth.cd2d(2000, 1.0)
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
+        y = ppg.apply_phi(Ad, roots, v)
+    elif name == "p_cd3d_160_f32":
+        A = synth.cd3d(160, (0.8, 0.4, 0.2))
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals, dtype=torch.float32)
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda().float()
+        y = ppg.apply_poly(Ad, roots, v)
+    else:
+        raise SystemExit("unknown profile case " + name)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "n": A.n, "nnz": A.nnz,
+                      "finite": bool(torch.isfinite(y).all().item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,7 +431,10 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=200)
     ap.add_argument("--ref-cycles", type=int, default=4)
     ap.add_argument("--oracle-sample", type=int, default=None)
+    ap.add_argument("--profile-case", default=None)
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args.profile_case)
     if args.oracle_sample is not None:
         print(json.dumps(oracle_sample(args.oracle_sample)))
         return 0
