@@ -50,6 +50,10 @@ extern "C" {
 #define PPG_ERR_CAPACITY     -6   /* ppg_roots arrays too small; n_total = needed */
 #define PPG_ERR_EIG          -7   /* Hessenberg QR did not converge */
 #define PPG_ERR_NOMEM        -8   /* device scratch allocation failed */
+#define PPG_ERR_TOO_LARGE    -9   /* n above PPG_NOALLOC_MAX_N (ppg_apply_poly_noalloc) */
+
+/* Largest n that ppg_apply_poly_noalloc accepts (its fixed work area). */
+#define PPG_NOALLOC_MAX_N 1048576
 
 /* dtypes */
 #define PPG_F64 0
@@ -175,6 +179,28 @@ int32_t ppg_build_poly(const ppg_csr* A, int32_t d, const double* v0,
  * float.  Asynchronous. */
 int32_t ppg_apply_poly(const ppg_csr* A, const ppg_roots* r, const void* v,
                        void* y, void* stream);
+
+/* y = p(A) v exactly as ppg_apply_poly computes it, for callers that cannot
+ * allocate device memory at call time: their GPU memory is already held by
+ * another allocator (for example a framework's caching allocator that has
+ * reserved the whole device), or an allocation or free would synchronise
+ * the device or could fail under memory pressure in the middle of their
+ * work.  The paper has no counterpart: this is a deployment variant.
+ *
+ * It allocates nothing.  Its three work vectors live in one fixed array of
+ * 3 * PPG_NOALLOC_MAX_N doubles (24 MiB) compiled into the library; every
+ * GPU that loads the library holds that array until the process exits.
+ * n > PPG_NOALLOC_MAX_N is rejected with PPG_ERR_TOO_LARGE before any work
+ * is enqueued.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents (nothing in it needs to start at zero:
+ * each call writes every slot before reading it), so calls whose GPU work
+ * overlaps -- on different streams or host threads -- race and give wrong
+ * results; serialise them.  v and y are caller-owned device vectors as for
+ * ppg_apply_poly.  Asynchronous on `stream`. */
+int32_t ppg_apply_poly_noalloc(const ppg_csr* A, const ppg_roots* r,
+                               const void* v, void* y, void* stream);
 
 /* y = phi(A) v = v - pi(A) v by Algorithm 1: d fused SpMV-root passes.
  * Asynchronous. */

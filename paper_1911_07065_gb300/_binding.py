@@ -24,8 +24,9 @@ STATUS = {
     0: "PPG_OK", 1: "PPG_NOT_CONVERGED", 2: "PPG_LUCKY_BREAKDOWN",
     -1: "PPG_ERR_ARG", -2: "PPG_ERR_CSR", -3: "PPG_ERR_SINGULAR_H",
     -4: "PPG_ERR_NONFINITE", -5: "PPG_ERR_CUDA", -6: "PPG_ERR_CAPACITY",
-    -7: "PPG_ERR_EIG", -8: "PPG_ERR_NOMEM",
+    -7: "PPG_ERR_EIG", -8: "PPG_ERR_NOMEM", -9: "PPG_ERR_TOO_LARGE",
 }
+NOALLOC_MAX_N = 1048576
 
 
 class ppg_csr(C.Structure):
@@ -84,6 +85,8 @@ def _load():
                                    C.POINTER(ppg_roots), P_F64, c_vp]),
         "ppg_apply_poly": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
         "ppg_apply_phi": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
+        "ppg_apply_poly_noalloc": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp,
+                                           c_vp, c_vp]),
         "ppg_spmv": (c_i32, [C.POINTER(ppg_csr), c_vp, c_vp, c_vp]),
         "ppg_solve": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_i32,
                               c_f64, C.POINTER(ppg_opts), C.POINTER(ppg_stats), c_vp]),
@@ -111,7 +114,7 @@ EXPORTS = (
     "ppg_harmonic_ritz", "ppg_leja_order", "ppg_add_roots", "ppg_roots_from_hessenberg",
     "ppg_csr_validate_host", "ppg_build_poly", "ppg_apply_poly", "ppg_apply_phi",
     "ppg_spmv", "ppg_solve", "ppg_solve_flex", "ppg_stability_check",
-    "ppg_csr_transpose", "ppg_adjoint_vals_grad",
+    "ppg_csr_transpose", "ppg_adjoint_vals_grad", "ppg_apply_poly_noalloc",
 )
 
 

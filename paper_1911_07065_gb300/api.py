@@ -110,6 +110,17 @@ def apply_poly(A: CSR, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor
     return y
 
 
+def apply_poly_noalloc(A: CSR, roots: Roots, v: torch.Tensor, out: torch.Tensor,
+                       stream=None) -> torch.Tensor:
+    """y = p(A) v through the entry point that allocates no device memory
+    (for callers that cannot allocate: see ppg_apply_poly_noalloc in the C
+    header).  ``out`` must be given; n <= 1048576; calls must not overlap."""
+    _need_cuda(v, out)
+    check(lib.ppg_apply_poly_noalloc(A.ref(), roots.ref(), _ptr(v), _ptr(out), _stream(stream)),
+          "ppg_apply_poly_noalloc")
+    return out
+
+
 def apply_phi(A: CSR, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor] = None,
               stream=None) -> torch.Tensor:
     """y = phi(A) v (Algorithm 1) in A's dtype."""

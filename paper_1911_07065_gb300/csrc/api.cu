@@ -579,6 +579,7 @@ const char* ppg_strerror(int32_t code) {
         case PPG_ERR_CAPACITY: return "roots capacity too small";
         case PPG_ERR_EIG: return "Hessenberg QR did not converge";
         case PPG_ERR_NOMEM: return "device scratch allocation failed";
+        case PPG_ERR_TOO_LARGE: return "n exceeds PPG_NOALLOC_MAX_N (1048576), the fixed work area of ppg_apply_poly_noalloc";
         default: return "unknown status";
     }
 }
