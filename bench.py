@@ -389,9 +389,11 @@ PROFILE_ROOTS = (7.5, 0.35, 3.9, 6.1, 1.6, 4.9)   # real roots spread over the s
 
 
 def run_profile_case(name):
-    """A few launches of the fused SpMV-root kernel for an ncu capture:
+    """A few launches of one kernel family for an ncu capture:
     ``phi_cd2d_2000``: Algorithm 1 on 2-D convection-diffusion 2000 x 2000
     (n = 4e6, FP64; the matrix and vectors exceed L2), six real roots;
+    ``arnoldi_cd2d_2000``: the degree-30 polynomial construction on it (CGS2);
+    ``phi_cd2d_1000``: two applications of the benchmark's own polynomial;
     ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix."""
     import numpy as np
     import torch
@@ -405,6 +407,24 @@ def run_profile_case(name):
         Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
         y = ppg.apply_phi(Ad, roots, v)
+    elif name == "phi_cd2d_1000":
+        # the benchmark's own matrix and degree-40 polynomial: build it, then
+        # apply phi twice (the second application runs with A warm in L2)
+        P = synth.problem(WORKLOAD)
+        A = P.A
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
+        R = ppg.build_poly(Ad, P.d, torch.from_numpy(P.v0).cuda())
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
+        y = ppg.apply_phi(Ad, R, v)
+        y = ppg.apply_phi(Ad, R, y)
+    elif name == "arnoldi_cd2d_2000":
+        # the polynomial's Arnoldi (d = 30) on n = 4e6: CGS2 passes over up to
+        # 31 basis columns of 32 MB
+        A = synth.cd2d(2000, 1.0)
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
+        R = ppg.build_poly(Ad, 30, v)
+        y = torch.from_numpy(R.re[: R.n_total].copy())
     elif name == "p_cd3d_160_f32":
         A = synth.cd3d(160, (0.8, 0.4, 0.2))
         Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals, dtype=torch.float32)

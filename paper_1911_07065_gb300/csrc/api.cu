@@ -121,6 +121,7 @@ int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr, const int
                  const T* vals, int32_t n, int64_t nnz, const Buffers& bufs, cudaStream_t s,
                  double* bytes_out) {
     double bytes = 0.0;
+    const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3);
     for (const Step& st : plan) {
         if (st.op == OP_AXPY) {
             const bool pz = st.flags & F_PZERO;
@@ -143,7 +144,7 @@ int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr, const int
         a.c1 = (T)st.c1;
         a.c2 = (T)st.c2;
         a.c3 = (T)st.c3;
-        a.flags = st.flags;
+        a.flags = st.flags | keep;
         a.part = nullptr;
         int32_t rc = launch_step<T>(st.op, a, s);
         if (rc < 0) return rc;
@@ -211,6 +212,19 @@ static int32_t setup_device_pool() {
 }
 
 static int64_t pad_ld(int32_t n) { return ((int64_t)n + 63) / 64 * 64; }
+
+// Pinned host buffer for the per-step status read (one per host thread,
+// allocated on first use and kept for the life of the process).
+static int32_t status_buffer(double** out) {
+    static thread_local double* buf = nullptr;
+    if (!buf) {
+        void* p = nullptr;
+        PPG_CUDA(cudaMallocHost(&p, 8 * sizeof(double)));
+        buf = (double*)p;
+    }
+    *out = buf;
+    return PPG_OK;
+}
 
 static int32_t check_csr(const ppg_csr* A, int dtype_required) {
     if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && (!A->colind || !A->vals)))
@@ -301,8 +315,9 @@ static int32_t cgs2_column(SolveCore& c, int j, double* w, bool with_self, Event
     const int32_t n = c.A64->n;
     if (ev) ev->start(c.s);
     PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, with_self, c.ows.h1, c.ows, c.s));
-    PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h1, 1, c.ows.h2, c.ows, c.s));
-    PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h2, 2, c.ows.nrm, c.ows, c.s));
+    PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h1, false, nullptr, c.ows, c.s));
+    PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, false, c.ows.h2, c.ows, c.s));
+    PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h2, true, c.ows.nrm, c.ows, c.s));
     return PPG_OK;
 }
 
@@ -363,7 +378,8 @@ static int32_t run_solve(SolveCore& c) {
     PPG_TRY(ev_orth.init(c.opts.timing != 0));
 
     c.st = ppg_stats{};
-    double scal_h[8];
+    double* scal_h = nullptr;
+    PPG_TRY(status_buffer(&scal_h));
     int nparts = 0;
 
     // ||b||
@@ -391,6 +407,7 @@ static int32_t run_solve(SolveCore& c) {
         a.colind = c.A64->colind;
         a.vals = (const double*)c.A64->vals;
         a.n = n;
+        a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
         if (c.opts.x0_given) {
             a.x = c.x;
             a.a0 = c.b;
@@ -456,6 +473,7 @@ static int32_t run_solve(SolveCore& c) {
                 a.colind = c.A64->colind;
                 a.vals = (const double*)c.A64->vals;
                 a.n = n;
+                a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
                 a.x = c.u;
                 a.o0 = w;
                 int32_t g = launch_step<double>(OP_SPMV, a, s);
@@ -477,6 +495,7 @@ static int32_t run_solve(SolveCore& c) {
                 a.colind = c.A64->colind;
                 a.vals = (const double*)c.A64->vals;
                 a.n = n;
+                a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
                 a.x = vj;
                 a.o0 = w;
                 int32_t g = launch_step<double>(OP_SPMV, a, s);
@@ -532,6 +551,7 @@ static int32_t run_solve(SolveCore& c) {
         a.colind = c.A64->colind;
         a.vals = (const double*)c.A64->vals;
         a.n = n;
+        a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
         a.x = c.x;
         a.a0 = c.b;
         a.o0 = c.V;
@@ -652,12 +672,14 @@ int32_t ppg_spmv(const ppg_csr* A, const void* x, void* y, void* stream) {
         StepArgs<double> a{};
         a.rowptr = A->rowptr; a.colind = A->colind; a.vals = (const double*)A->vals; a.n = A->n;
         a.x = (const double*)x; a.o0 = (double*)y;
+        a.flags = keep_a_flag(A->n, A->nnz, 8, 2);
         int32_t g = launch_step<double>(OP_SPMV, a, s);
         return g < 0 ? g : PPG_OK;
     }
     StepArgs<float> a{};
     a.rowptr = A->rowptr; a.colind = A->colind; a.vals = (const float*)A->vals; a.n = A->n;
     a.x = (const float*)x; a.o0 = (float*)y;
+    a.flags = keep_a_flag(A->n, A->nnz, 4, 2);
     int32_t g = launch_step<float>(OP_SPMV, a, s);
     return g < 0 ? g : PPG_OK;
 }
@@ -752,6 +774,7 @@ int32_t ppg_build_poly(const ppg_csr* A, int32_t d, const double* v0, const ppg_
         a.colind = A->colind;
         a.vals = (const double*)A->vals;
         a.n = n;
+        a.flags = keep_a_flag(a.n, A->nnz, 8, 3);
         a.x = vj;
         a.o0 = w;
         int32_t g = launch_step<double>(OP_SPMV, a, s);
@@ -857,6 +880,7 @@ int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r, const double* 
     a.colind = A->colind;
     a.vals = vals;
     a.n = n;
+    a.flags = keep_a_flag(n, A->nnz, 8, 3);
     a.x = y;
     a.a0 = b;
     a.o0 = r1;

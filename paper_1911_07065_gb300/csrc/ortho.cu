@@ -3,211 +3,205 @@
 // solution update V y, norms and scaling.
 //
 // The basis V is column-major with leading dimension ldv (>= n, padded so
-// each column starts on a 512-byte boundary).  CGS2 runs as three passes
-// over the active columns:
-//   pass 1  h1 = V^T w                          (k_cgs<0>)
-//   pass 2  w -= V h1, then h2 = V^T w          (k_cgs<1>)
-//   pass 3  w -= V h2, then ||w||^2             (k_cgs<2>)
-// Passes 2 and 3 stage a tile of ORTHO_TR rows x ncol columns of V in
-// shared memory, so the column sums and the dot products of the same tile
-// read V from HBM once.  Each pass ends with a deterministic reduction of
-// the per-CTA partial sums done by the last CTA to finish (no extra
-// launch; the counter resets itself).
+// each column starts on a 512-byte boundary).  Classical Gram-Schmidt
+// applied twice runs as four streaming passes over the active columns:
+//   h1 = V^T w ;  w -= V h1 ;  h2 = V^T w ;  w -= V h2 (and ||w||^2)
+// Each pass spends exactly one FP64 fused multiply-add per element of V --
+// on GB300 the FP64 pipe (about two operations per clock per SM), not HBM,
+// is the tighter bound for this work -- and keeps many independent loads in
+// flight per thread.  The dot pass accumulates eight columns per thread in
+// registers, reduces them across the warp with an exchange tree of nine
+// shuffles for all eight, and the last CTA to finish sums the per-CTA
+// partials in a fixed order (deterministic; the counter resets itself, no
+// waiting, no extra launch).
 #include "ppg_common.cuh"
 
 namespace ppg {
 
 constexpr int ORTHO_THREADS = 256;
-constexpr int ORTHO_TR = 32;                          // rows per tile
 constexpr int ORTHO_WARPS = ORTHO_THREADS / 32;
+constexpr int DOT_CH = 8;                 // columns per register chunk
+constexpr int PART_STRIDE = ORTHO_MAXC + 2;
 
 int ortho_grid(int32_t n) {
-    int tiles = (n + ORTHO_TR - 1) / ORTHO_TR;
-    return max(1, min(tiles, 152 * 4));
+    const int per = ORTHO_THREADS * 8;   // at least ~8 rows per thread
+    return max(1, min((n + per - 1) / per, 152 * 2));
 }
 
-size_t ortho_part_doubles(int grid) { return (size_t)grid * (ORTHO_MAXC + 2); }
+size_t ortho_part_doubles(int grid) { return (size_t)max(grid, 152 * 8) * PART_STRIDE; }
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     return v;
 }
 
-// Reduce part[b * stride + c] over b for c < nvals, in block order; result
-// to out[c].  Called by every thread of the last CTA.
-__device__ void final_reduce(const double* part, int nblocks, int stride, int nvals,
-                             double* out) {
+// Sum each of v[0..7] over the 32 lanes.  Afterwards lane l with (l & 3) == 0
+// holds the total of value l >> 2 in v[0].
+__device__ __forceinline__ void warp_reduce8(double v[8], int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 16;
+        const double send = hi ? v[i] : v[i + 4];
+        const double keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 8;
+        const double send = hi ? v[i] : v[i + 2];
+        const double keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool hi = lane & 4;
+        const double send = hi ? v[0] : v[1];
+        const double keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Reduce part[b * PART_STRIDE + c] over b < nblocks for c < nvals, in block
+// order, into out[c].  Called by every thread of the last CTA.
+__device__ void final_reduce(const double* part, int nblocks, int nvals, double* out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = warp; c < nvals; c += ORTHO_WARPS) {
         double s = 0.0;
-        for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * stride + c);
+        for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * PART_STRIDE + c);
         s = warp_sum(s);
         if (lane == 0) out[c] = s;
     }
 }
 
-// MODE 0: dots of w with ncol columns (+ w.w if with_self)
-// MODE 1: w -= V hin ; dots of the new w with ncol columns
-// MODE 2: w -= V hin ; ||w||^2
-// Warp wp accumulates columns wp, wp + 8, ...: at most CPW of them, so
-// ncol <= 8 * CPW.
-template <int MODE, int ORTHO_CPW>
-__global__ void __launch_bounds__(ORTHO_THREADS)
-k_cgs(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
-      const double* __restrict__ hin, int with_self, double* part, unsigned* counter,
-      double* hout) {
-    // shared layout (doubles): sV [tilecols][ORTHO_TR] | sw [ORTHO_TR] |
-    // sh [ORTHO_MAXC] | sred [ORTHO_WARPS][ORTHO_TR]; MODE 0 stages no V tile
-    extern __shared__ double smem[];
-    const int tilecols = (MODE == 0) ? 0 : ncol;
-    double* sV = smem;
-    double* sw = sV + (size_t)tilecols * ORTHO_TR;
-    double* sh = sw + ORTHO_TR;
-    double* sred = sh + ORTHO_MAXC;
+__device__ __forceinline__ bool last_block_done(unsigned* counter) {
     __shared__ bool am_last;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (MODE != 0)
-        for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = hin[c];
-
-    double acc[ORTHO_CPW];
-#pragma unroll
-    for (int q = 0; q < ORTHO_CPW; ++q) acc[q] = 0.0;
-    double accself = 0.0;
-
-    const int64_t ntiles = ((int64_t)n + ORTHO_TR - 1) / ORTHO_TR;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t r0 = t * ORTHO_TR;
-        const int rows = (int)(((int64_t)n - r0) < ORTHO_TR ? ((int64_t)n - r0) : ORTHO_TR);
-        __syncthreads();
-        if (MODE == 0) {
-            // w tile only; V is read straight from global below
-            if (tid < ORTHO_TR) sw[tid] = (tid < rows) ? w[r0 + tid] : 0.0;
-            __syncthreads();
-            const double wv = sw[lane];
-#pragma unroll
-            for (int q = 0; q < ORTHO_CPW; ++q) {
-                const int c = warp + q * ORTHO_WARPS;
-                if (c < ncol && lane < rows) acc[q] += __ldcs(V + c * ldv + r0 + lane) * wv;
-            }
-            if (with_self && warp == 0) accself += wv * wv;
-        } else {
-            for (int e = tid; e < ncol * ORTHO_TR; e += ORTHO_THREADS) {
-                const int c = e / ORTHO_TR, i = e % ORTHO_TR;
-                sV[e] = (i < rows) ? __ldcs(V + c * ldv + r0 + i) : 0.0;
-            }
-            if (tid < ORTHO_TR) sw[tid] = (tid < rows) ? w[r0 + tid] : 0.0;
-            __syncthreads();
-            // s_i = sum_c V[c][i] hin[c]: warp wp takes columns c = wp (mod 8)
-            double s = 0.0;
-            for (int c = warp; c < ncol; c += ORTHO_WARPS) s += sV[c * ORTHO_TR + lane] * sh[c];
-            sred[warp * ORTHO_TR + lane] = s;
-            __syncthreads();
-            if (tid < ORTHO_TR) {
-                double tot = 0.0;
-#pragma unroll
-                for (int k = 0; k < ORTHO_WARPS; ++k) tot += sred[k * ORTHO_TR + tid];
-                const double nw = sw[tid] - tot;
-                sw[tid] = nw;
-                if (tid < rows) w[r0 + tid] = nw;
-            }
-            __syncthreads();
-            const double wv = sw[lane];
-            if (MODE == 1) {
-#pragma unroll
-                for (int q = 0; q < ORTHO_CPW; ++q) {
-                    const int c = warp + q * ORTHO_WARPS;
-                    if (c < ncol) acc[q] += sV[c * ORTHO_TR + lane] * wv;
-                }
-            } else if (warp == 0) {
-                accself += wv * wv;
-            }
-        }
-    }
-
-    // per-CTA partials: part[blockIdx.x * stride + c]
-    const int stride = ORTHO_MAXC + 2;
-    double* mypart = part + (size_t)blockIdx.x * stride;
-    if (MODE != 2) {
-#pragma unroll
-        for (int q = 0; q < ORTHO_CPW; ++q) {
-            const int c = warp + q * ORTHO_WARPS;
-            const double v = warp_sum(acc[q]);
-            if (c < ncol && lane == 0) mypart[c] = v;
-        }
-    }
-    const int nvals = (MODE == 2) ? 1 : ncol + ((MODE == 0 && with_self) ? 1 : 0);
-    if (MODE == 2 || (MODE == 0 && with_self)) {
-        const double v = warp_sum(accself);
-        if (warp == 0 && lane == 0) mypart[(MODE == 2) ? 0 : ncol] = v;
-    }
     __threadfence();
     __syncthreads();
-    if (tid == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return am_last;
+}
+
+// hout[c] = sum_r V[c][r] w[r] for c < ncol, and hout[ncol] = w.w when
+// with_self.  Grid: x = row blocks (grid-stride), y = chunks of eight
+// columns, so every column chunk streams in parallel.
+__global__ void __launch_bounds__(ORTHO_THREADS)
+k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __restrict__ w,
+       int32_t n, int with_self, double* part, unsigned* counter, double* hout) {
+    __shared__ double sred[ORTHO_WARPS][DOT_CH];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nvals = ncol + (with_self ? 1 : 0);
+    const int c0 = blockIdx.y * DOT_CH;
+    const double* col[DOT_CH];
+#pragma unroll
+    for (int q = 0; q < DOT_CH; ++q) {
+        const int c = c0 + q;
+        col[q] = (c < ncol) ? V + c * ldv : ((c == ncol && with_self) ? w : nullptr);
+    }
+    double acc[DOT_CH];
+#pragma unroll
+    for (int q = 0; q < DOT_CH; ++q) acc[q] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
+    int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
+    for (; r + stride < n; r += 2 * stride) {   // two rows per trip: 18 loads in flight
+        const double w0 = w[r], w1 = w[r + stride];
+#pragma unroll
+        for (int q = 0; q < DOT_CH; ++q) {
+            if (col[q]) {
+                const double a0 = __ldcs(col[q] + r), a1 = __ldcs(col[q] + r + stride);
+                acc[q] = fma(a1, w1, fma(a0, w0, acc[q]));
+            }
+        }
+    }
+    if (r < n) {
+        const double w0 = w[r];
+#pragma unroll
+        for (int q = 0; q < DOT_CH; ++q)
+            if (col[q]) acc[q] = fma(__ldcs(col[q] + r), w0, acc[q]);
+    }
+    warp_reduce8(acc, lane);
+    if ((lane & 3) == 0) sred[warp][lane >> 2] = acc[0];
+    __syncthreads();
+    if (tid < DOT_CH && c0 + tid < nvals) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < ORTHO_WARPS; ++k) t += sred[k][tid];
+        part[(size_t)blockIdx.x * PART_STRIDE + c0 + tid] = t;
+    }
+    // the last CTA of the whole grid sums the partials of every column
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x * gridDim.y - 1);
     __syncthreads();
     if (am_last) {
         __threadfence();
-        final_reduce(part, gridDim.x, stride, nvals, hout);
+        final_reduce(part, gridDim.x, nvals, hout);
         if (tid == 0) *counter = 0u;
     }
 }
 
-// dynamic shared bytes for a launch staging `tilecols` columns of V (the
-// kernel's layout above; MODE 0 passes 0)
-static size_t cgs_smem(int tilecols) {
-    return sizeof(double) * ((size_t)tilecols * ORTHO_TR + ORTHO_TR + ORTHO_MAXC +
-                             ORTHO_WARPS * ORTHO_TR);
+// w[r] -= sum_c V[c][r] h[c]; with_norm: nout[0] = ||w||^2 afterwards
+__global__ void __launch_bounds__(ORTHO_THREADS)
+k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
+           const double* __restrict__ h, int with_norm, double* part, unsigned* counter,
+           double* nout) {
+    __shared__ double sh[ORTHO_MAXC];
+    __shared__ double sred[ORTHO_WARPS];
+    const int tid = threadIdx.x;
+    for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = h[c];
+    __syncthreads();
+    double nacc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
+    for (int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid; r < n; r += stride) {
+        double s0 = 0.0, s1 = 0.0;
+        int c = 0;
+        for (; c + 1 < ncol; c += 2) {
+            s0 = fma(__ldcs(V + c * ldv + r), sh[c], s0);
+            s1 = fma(__ldcs(V + (c + 1) * ldv + r), sh[c + 1], s1);
+        }
+        if (c < ncol) s0 = fma(__ldcs(V + c * ldv + r), sh[c], s0);
+        const double wn = w[r] - (s0 + s1);
+        w[r] = wn;
+        nacc = fma(wn, wn, nacc);
+    }
+    if (!with_norm) return;
+    nacc = warp_sum(nacc);
+    if ((tid & 31) == 0) sred[tid >> 5] = nacc;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int k = 0; k < ORTHO_WARPS; ++k) t += sred[k];
+        part[(size_t)blockIdx.x * PART_STRIDE] = t;
+    }
+    if (last_block_done(counter)) {
+        __threadfence();
+        final_reduce(part, gridDim.x, 1, nout);
+        if (tid == 0) *counter = 0u;
+    }
 }
 
-static int32_t set_smem_attrs() {
-    static bool done = false;   // per process; the attribute is per function
-    if (done) return PPG_OK;
-    const int mx = (int)cgs_smem(ORTHO_MAXC);
-    PPG_CUDA(cudaFuncSetAttribute(k_cgs<1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    PPG_CUDA(cudaFuncSetAttribute(k_cgs<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    PPG_CUDA(cudaFuncSetAttribute(k_cgs<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    PPG_CUDA(cudaFuncSetAttribute(k_cgs<2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    done = true;
-    return PPG_OK;
-}
-
-int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w,
-                       int32_t n, bool with_self, double* h_out, const OrthoWs& ws,
-                       cudaStream_t s) {
-    if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
-    PPG_TRY(set_smem_attrs());
-    if (ncol + 1 <= 8 * 8)
-        k_cgs<0, 8><<<ws.grid, ORTHO_THREADS, cgs_smem(0), s>>>(
-            V, ldv, ncol, const_cast<double*>(w), n, nullptr, with_self ? 1 : 0, ws.part,
-            ws.counter, h_out);
-    else
-        k_cgs<0, 32><<<ws.grid, ORTHO_THREADS, cgs_smem(0), s>>>(
-            V, ldv, ncol, const_cast<double*>(w), n, nullptr, with_self ? 1 : 0, ws.part,
-            ws.counter, h_out);
+int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, int32_t n,
+                       bool with_self, double* h_out, const OrthoWs& ws, cudaStream_t s) {
+    if (ncol < 1 || ncol + 1 > ORTHO_MAXC + 2) return PPG_ERR_ARG;
+    const int nvals = ncol + (with_self ? 1 : 0);
+    const dim3 grid(ws.grid, (nvals + DOT_CH - 1) / DOT_CH);
+    k_mdot<<<grid, ORTHO_THREADS, 0, s>>>(V, ldv, ncol, w, n, with_self ? 1 : 0, ws.part,
+                                          ws.counter, h_out);
     ++g_launches;
-    return check_launch("k_cgs<0>");
+    return check_launch("k_mdot");
 }
 
 int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int32_t n,
-                          const double* hin, int mode, double* h_out, const OrthoWs& ws,
-                          cudaStream_t s) {
+                          const double* hin, bool with_norm, double* nrm_out,
+                          const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
-    PPG_TRY(set_smem_attrs());
-    const bool small = ncol <= 8 * 8;
-    if (mode == 1 && small)
-        k_cgs<1, 8><<<ws.grid, ORTHO_THREADS, cgs_smem(ncol), s>>>(
-            V, ldv, ncol, w, n, hin, 0, ws.part, ws.counter + 1, h_out);
-    else if (mode == 1)
-        k_cgs<1, 32><<<ws.grid, ORTHO_THREADS, cgs_smem(ncol), s>>>(
-            V, ldv, ncol, w, n, hin, 0, ws.part, ws.counter + 1, h_out);
-    else if (small)
-        k_cgs<2, 8><<<ws.grid, ORTHO_THREADS, cgs_smem(ncol), s>>>(
-            V, ldv, ncol, w, n, hin, 0, ws.part, ws.counter + 2, h_out);
-    else
-        k_cgs<2, 32><<<ws.grid, ORTHO_THREADS, cgs_smem(ncol), s>>>(
-            V, ldv, ncol, w, n, hin, 0, ws.part, ws.counter + 2, h_out);
+    const int grid = max(1, min((n + ORTHO_THREADS - 1) / ORTHO_THREADS, 152 * 8));
+    k_gemv_sub<<<grid, ORTHO_THREADS, 0, s>>>(V, ldv, ncol, w, n, hin, with_norm ? 1 : 0,
+                                              ws.part, ws.counter + 1, nrm_out);
     ++g_launches;
-    return check_launch("k_cgs<1/2>");
+    return check_launch("k_gemv_sub");
 }
 
 // ---------------------------------------------------------------------------
@@ -217,17 +211,28 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
 __global__ void k_finish_column(GmresState st, int ldh, int j, const double* h1,
                                 const double* h2, const double* nrm, int givens,
                                 double bnorm, double brtol) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double* sc = st.scal;
+    // one warp stages the column and the rotations in shared memory, then
+    // one thread applies the j earlier rotations and makes the new one
+    __shared__ double col[ORTHO_MAXC + 1];
+    __shared__ double scs[ORTHO_MAXC], ssn[ORTHO_MAXC];
+    const int lane = threadIdx.x;
+    for (int i = lane; i <= j; i += 32) col[i] = h1[i] + h2[i];
+    if (givens)
+        for (int i = lane; i < j; i += 32) {
+            scs[i] = st.cs[i];
+            ssn[i] = st.sn[i];
+        }
     const double hn = sqrt(fmax(nrm[0], 0.0));
-    double col[ORTHO_MAXC + 1];
-    for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-    col[j + 1] = hn;
+    if (lane == 0) col[j + 1] = hn;
+    __syncwarp();
     if (st.Hraw)
-        for (int i = 0; i <= j + 1; ++i) st.Hraw[(size_t)j * ldh + i] = col[i];
-    bool brk = false;
+        for (int i = lane; i <= j + 1; i += 32) st.Hraw[(size_t)j * ldh + i] = col[i];
+    __syncwarp();
+    if (lane != 0) return;
+    double* sc = st.scal;
+    bool brk;
     if (brtol > 0.0) {
-        const double w0 = sqrt(fmax(h1[j + 1], 0.0));   // ||A v_j|| from pass 1
+        const double w0 = sqrt(fmax(h1[j + 1], 0.0));   // ||A v_j|| from the first dot pass
         brk = !(hn > brtol * w0);
     } else {
         brk = !(hn > 0.0);
@@ -240,11 +245,14 @@ __global__ void k_finish_column(GmresState st, int ldh, int j, const double* h1,
     sc[1] = hn;
     sc[2] = (hn > 0.0 && !brk) ? 1.0 / hn : 0.0;
     if (givens) {
+        double ci = col[0];
         for (int i = 0; i < j; ++i) {
-            const double t = st.cs[i] * col[i] + st.sn[i] * col[i + 1];
-            col[i + 1] = -st.sn[i] * col[i] + st.cs[i] * col[i + 1];
+            const double nxt = col[i + 1];
+            const double t = scs[i] * ci + ssn[i] * nxt;
+            ci = -ssn[i] * ci + scs[i] * nxt;
             col[i] = t;
         }
+        col[j] = ci;
         const double a = col[j], b = col[j + 1];
         const double r = hypot(a, b);
         double c = 1.0, s = 0.0;
@@ -252,7 +260,6 @@ __global__ void k_finish_column(GmresState st, int ldh, int j, const double* h1,
         st.cs[j] = c;
         st.sn[j] = s;
         col[j] = r;
-        col[j + 1] = 0.0;
         for (int i = 0; i <= j; ++i) st.R[(size_t)j * ldh + i] = col[i];
         const double gj = st.g[j];
         st.g[j + 1] = -s * gj;

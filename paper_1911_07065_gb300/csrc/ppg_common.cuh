@@ -54,6 +54,7 @@ enum StepFlag : int {
                    // P_PAIR2: o0 = a1 + c3 prod'
     F_PZERO = 2,   // P_*: the accumulator p starts at zero (a1 not read)
     F_NO_O1 = 4,   // P_PAIR1: tmp not needed afterwards
+    F_KEEP_A = 8,  // copy A with an L2 evict-last hint (A and the vectors fit in L2)
 };
 
 template <typename T>
@@ -77,6 +78,9 @@ struct StepArgs {
 // OP_RESID) or a negative status
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s);
+
+// F_KEEP_A when the matrix plus `nvec` work vectors fit comfortably in L2
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec);
 
 int32_t spmv_grid_blocks(int32_t n);
 
@@ -115,7 +119,7 @@ int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr,
 // ---------------------------------------------------------------------------
 
 struct OrthoWs {
-    double* part;       // [grid * (MAXC + 2)]
+    double* part;       // [ortho_part_doubles(grid)]
     unsigned* counter;  // [4] zero-initialised, self-resetting
     double* h1;         // [MAXC + 2]
     double* h2;         // [MAXC + 2]
@@ -132,9 +136,9 @@ size_t ortho_part_doubles(int grid);
 int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w,
                        int32_t n, bool with_self, double* h_out,
                        const OrthoWs& ws, cudaStream_t s);
-// w -= V hin ; then h_out = V^T w (mode 1) or h_out[0] = w.w (mode 2)
+// w -= V hin ; with_norm: nrm_out[0] = w.w afterwards
 int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w,
-                          int32_t n, const double* hin, int mode, double* h_out,
+                          int32_t n, const double* hin, bool with_norm, double* nrm_out,
                           const OrthoWs& ws, cudaStream_t s);
 
 struct GmresState {   // device, one per solve

@@ -2,37 +2,64 @@
 // polynomial (Algorithm 1: phi(A) v, Algorithm 3: p(A) v), plus the plain
 // SpMV and the residual b - A x.
 //
-// Layout: a CTA owns a tile of SPMV_ROWS consecutive rows.  It stages the
-// products vals[k] * x[colind[k]] of the tile's nonzeros in shared memory
-// with fully coalesced, streaming loads of vals/colind (consecutive threads
-// take consecutive k, so short rows of 5-7 entries cost no idle lanes),
-// then thread t sums row t of the tile and applies the root update in the
-// epilogue, reading and writing the row-aligned vectors once, coalesced.
-// Tiles whose nonzeros exceed the staging buffer are processed in chunks,
-// so any row length is handled.
+// Layout: a CTA owns a tile of SPMV_ROWS consecutive rows.  It copies the
+// tile's column indices and values into shared memory with asynchronous,
+// fully coalesced copies (cp.async; consecutive threads take consecutive
+// nonzeros, so short rows of 5-7 entries leave no lane idle), then thread t
+// walks row t of the tile with one fused multiply-add per nonzero,
+// acc = fma(val, x[col], acc), and applies the root update in the epilogue,
+// reading and writing the row-aligned vectors once, coalesced.  Tiles whose
+// nonzeros exceed the staging buffer are processed in chunks, so any row
+// length is handled.
+//
+// GB300 executes about two FP64 operations per clock per SM, so in FP64 the
+// multiply-adds, not only the bytes, bound this kernel: one FMA per nonzero
+// is the minimum and the epilogues use fused forms.
+//
+// L2 policy: when the matrix and the chain's vectors fit in L2, the matrix is
+// copied with an evict-last hint and stays resident across the roots of a
+// chain (every root reads the same A); otherwise with evict-first, so that
+// streaming A does not push the vectors out.
 #include "ppg_common.cuh"
 
 namespace ppg {
 
 constexpr int SPMV_ROWS = 256;      // rows per CTA = threads per CTA
-constexpr int SPMV_CHUNK_BYTES = 16384;
+constexpr int SPMV_CHUNK = 2048;    // nonzeros staged per chunk
 
-template <typename T>
-__device__ __forceinline__ T ld_stream(const T* p) {
-    return __ldcs(p);   // read-once data: evict-first
+__device__ __forceinline__ uint64_t l2_policy(int keep) {
+    uint64_t p;
+    if (keep)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, uint64_t pol) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(s),
+                 "l"(gmem), "n"(BYTES), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 template <typename T, int OP>
 __global__ void __launch_bounds__(SPMV_ROWS)
 k_spmv_step(const StepArgs<T> a) {
-    constexpr int CHUNK = SPMV_CHUNK_BYTES / sizeof(T);
-    __shared__ T sprod[CHUNK];
+    __shared__ T sval[SPMV_CHUNK];
+    __shared__ int32_t scol[SPMV_CHUNK];
     __shared__ int32_t srp[SPMV_ROWS + 1];
     __shared__ double sred[SPMV_ROWS / 32];
 
     const int64_t row0 = (int64_t)blockIdx.x * SPMV_ROWS;
     const int tid = threadIdx.x;
     const int nrows = (int)(((int64_t)a.n - row0) < SPMV_ROWS ? ((int64_t)a.n - row0) : SPMV_ROWS);
+    const uint64_t pol = l2_policy(a.flags & F_KEEP_A);
     for (int i = tid; i <= nrows; i += SPMV_ROWS) srp[i] = __ldg(a.rowptr + row0 + i);
     __syncthreads();
     const int32_t k0 = srp[0];
@@ -40,59 +67,81 @@ k_spmv_step(const StepArgs<T> a) {
     const int32_t my_lo = (tid < nrows) ? srp[tid] : k1;
     const int32_t my_hi = (tid < nrows) ? srp[tid + 1] : k1;
 
+    // The epilogue's row-aligned inputs do not depend on the product: load
+    // them now, so their latency overlaps the staging and the gathers.
+    const bool live = tid < nrows;
+    const int64_t rr = row0 + tid;
+    T e0 = T(0), e1 = T(0), e2 = T(0);
+    if (live) {
+        if (a.a0) e0 = __ldg(a.a0 + rr);
+        if (a.a1 && !(a.flags & F_PZERO)) e1 = a.a1[rr];
+        if (a.a2 && (a.flags & F_FINAL)) e2 = __ldg(a.a2 + rr);
+    }
+
     T acc = T(0);
-    for (int32_t c0 = k0; c0 < k1; c0 += CHUNK) {
-        const int32_t c1 = min(k1, c0 + CHUNK);
-#pragma unroll 4
+    for (int32_t c0 = k0; c0 < k1; c0 += SPMV_CHUNK) {
+        const int32_t c1 = min(k1, c0 + SPMV_CHUNK);
         for (int32_t k = c0 + tid; k < c1; k += SPMV_ROWS) {
-            const int32_t col = ld_stream(a.colind + k);
-            const T v = ld_stream(a.vals + k);
-            sprod[k - c0] = v * __ldg(a.x + col);
+            cp_async<sizeof(T)>(sval + (k - c0), a.vals + k, pol);
+            cp_async<4>(scol + (k - c0), a.colind + k, pol);
         }
+        cp_async_wait_all();
         __syncthreads();
-        const int32_t lo = max(my_lo, c0);
-        const int32_t hi = min(my_hi, c1);
-        for (int32_t k = lo; k < hi; ++k) acc += sprod[k - c0];
+        const int32_t lo = max(my_lo, c0) - c0;
+        const int32_t hi = min(my_hi, c1) - c0;
+        // exactly one FMA per nonzero (GB300 issues two FP64 operations per
+        // clock per SM), with the gathers of four nonzeros in flight before
+        // their multiply-adds; summation stays in column order
+        int32_t k = lo;
+        for (; k + 4 <= hi; k += 4) {
+            const T v0 = sval[k], v1 = sval[k + 1], v2 = sval[k + 2], v3 = sval[k + 3];
+            const T x0 = __ldg(a.x + scol[k]), x1 = __ldg(a.x + scol[k + 1]);
+            const T x2 = __ldg(a.x + scol[k + 2]), x3 = __ldg(a.x + scol[k + 3]);
+            acc = fma(v0, x0, acc);
+            acc = fma(v1, x1, acc);
+            acc = fma(v2, x2, acc);
+            acc = fma(v3, x3, acc);
+        }
+#pragma unroll 1
+        for (; k < hi; ++k) acc = fma(sval[k], __ldg(a.x + scol[k]), acc);
         __syncthreads();
     }
 
     double sq = 0.0;
-    if (tid < nrows) {
-        const int64_t r = row0 + tid;
+    if (live) {
+        const int64_t r = rr;
         const T s = acc;
         if constexpr (OP == OP_SPMV) {
             a.o0[r] = s;
         } else if constexpr (OP == OP_RESID) {
-            const T v = __ldg(a.a0 + r) - s;
+            const T v = e0 - s;
             a.o0[r] = v;
             sq = (double)v * (double)v;
         } else if constexpr (OP == OP_PHI_REAL) {
-            const T pin = __ldg(a.a0 + r) - a.c1 * s;
-            a.o0[r] = (a.flags & F_FINAL) ? __ldg(a.a2 + r) - pin : pin;
+            const T pin = fma(-a.c1, s, e0);
+            a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
         } else if constexpr (OP == OP_PHI_PAIR2) {
-            const T pin = a.a1[r] + a.c2 * (s - a.c1 * __ldg(a.a0 + r));
-            a.o0[r] = (a.flags & F_FINAL) ? __ldg(a.a2 + r) - pin : pin;
+            // pi' = pi + c2 (A prod - 2a prod)
+            const T t = fma(-a.c1, e0, s);
+            const T pin = fma(a.c2, t, e1);
+            a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
         } else if constexpr (OP == OP_P_REAL) {
-            const T pr = __ldg(a.a0 + r);
-            const T pold = (a.flags & F_PZERO) ? T(0) : a.a1[r];
-            const T pnew = pold + a.c1 * pr;
-            const T prodn = pr - a.c1 * s;
+            const T pnew = (a.flags & F_PZERO) ? a.c1 * e0 : fma(a.c1, e0, e1);
+            const T prodn = fma(-a.c1, s, e0);
             if (a.flags & F_FINAL) {
-                a.o0[r] = pnew + a.c3 * prodn;
+                a.o0[r] = fma(a.c3, prodn, pnew);
             } else {
                 a.o0[r] = pnew;
                 a.o1[r] = prodn;
             }
         } else if constexpr (OP == OP_P_PAIR1) {
-            const T pr = __ldg(a.a0 + r);
-            const T tmp = a.c1 * pr - s;
-            const T pold = (a.flags & F_PZERO) ? T(0) : a.a1[r];
-            a.o0[r] = pold + a.c2 * tmp;
+            const T tmp = fma(a.c1, e0, -s);
+            a.o0[r] = (a.flags & F_PZERO) ? a.c2 * tmp : fma(a.c2, tmp, e1);
             if (!(a.flags & F_NO_O1)) a.o1[r] = tmp;
         } else if constexpr (OP == OP_P_PAIR2) {
-            const T prodn = __ldg(a.a0 + r) - a.c2 * s;
+            const T prodn = fma(-a.c2, s, e0);
             if (a.flags & F_FINAL) {
-                a.o0[r] = a.a1[r] + a.c3 * prodn;
+                a.o0[r] = fma(a.c3, prodn, e1);
             } else {
                 a.o0[r] = prodn;
             }
@@ -112,6 +161,20 @@ k_spmv_step(const StepArgs<T> a) {
 }
 
 int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
+
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec) {
+    static int l2_bytes = -1;   // L2 size of the device first used (one GPU per process)
+    if (l2_bytes < 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+            v = 0;
+        cudaGetLastError();
+        l2_bytes = v;
+    }
+    const double bytes = (double)nnz * (elem + 4) + 4.0 * (n + 1) + (double)nvec * n * elem;
+    return bytes <= 0.8 * (double)l2_bytes ? F_KEEP_A : 0;
+}
 
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s) {
