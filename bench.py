@@ -351,6 +351,8 @@ def run_ours(args, rank, local, world):
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "iters": st["iters"], "cycles": st["cycles"], "mvps": st["mvps"], "dots": st["dots"],
+        "solve_breakdown_ms": {"spmv_root_chains": round(st["poly_ms"], 3),
+                               "cgs2_givens": round(st["ortho_ms"], 3)},
         "true_relres": rel, "converged": bool(st["converged"]),
         "roofline": {"bound": "hbm", "kernel": "k_spmv_step (fused SpMV-root, Alg 1/3)",
                      "achieved": round(achieved, 1) if achieved else None,

@@ -162,6 +162,25 @@ k_spmv_step(const StepArgs<T> a) {
 
 int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
 
+// Reserve L2 for evict-last (persisting) lines, once per process: without a
+// set-aside the evict-last hint is treated as normal.  This is a limit of
+// this process's context on its current device; it ends with the process.
+static void reserve_l2_for(size_t bytes) {
+    static size_t reserved = 0;
+    if (bytes <= reserved) return;
+    int dev = 0, maxp = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        maxp <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t want = bytes < (size_t)maxp ? bytes : (size_t)maxp;
+    if (want > reserved && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
+        reserved = want;
+    cudaGetLastError();
+}
+
 int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec) {
     static int l2_bytes = -1;   // L2 size of the device first used (one GPU per process)
     if (l2_bytes < 0) {
@@ -172,8 +191,11 @@ int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec) {
         cudaGetLastError();
         l2_bytes = v;
     }
-    const double bytes = (double)nnz * (elem + 4) + 4.0 * (n + 1) + (double)nvec * n * elem;
-    return bytes <= 0.8 * (double)l2_bytes ? F_KEEP_A : 0;
+    const double a_bytes = (double)nnz * (elem + 4) + 4.0 * (n + 1);
+    const double bytes = a_bytes + (double)nvec * n * elem;
+    if (!(bytes <= 0.8 * (double)l2_bytes)) return 0;
+    reserve_l2_for((size_t)(a_bytes * 1.05));
+    return F_KEEP_A;
 }
 
 template <typename T>
