@@ -16,6 +16,10 @@
 // multiply-adds, not only the bytes, bound this kernel: one FMA per nonzero
 // is the minimum and the epilogues use fused forms.
 //
+// Consecutive steps overlap: each is launched as a programmatic dependent of
+// the previous one and stages its share of the matrix before it waits for
+// the previous step's vectors.
+//
 // L2 policy: when the matrix and the chain's vectors fit in L2, the matrix is
 // copied with an evict-last hint and stays resident across the roots of a
 // chain (every root reads the same A); otherwise with evict-first, so that
@@ -60,12 +64,25 @@ k_spmv_step(const StepArgs<T> a) {
     const int tid = threadIdx.x;
     const int nrows = (int)(((int64_t)a.n - row0) < SPMV_ROWS ? ((int64_t)a.n - row0) : SPMV_ROWS);
     const uint64_t pol = l2_policy(a.flags & F_KEEP_A);
+    // Programmatic dependent launch: the next step in the stream may start
+    // now; everything up to griddepcontrol.wait reads only the matrix, which
+    // no step writes, so it overlaps the previous step's tail.
+    asm volatile("griddepcontrol.launch_dependents;");
     for (int i = tid; i <= nrows; i += SPMV_ROWS) srp[i] = __ldg(a.rowptr + row0 + i);
     __syncthreads();
     const int32_t k0 = srp[0];
     const int32_t k1 = srp[nrows];
     const int32_t my_lo = (tid < nrows) ? srp[tid] : k1;
     const int32_t my_hi = (tid < nrows) ? srp[tid + 1] : k1;
+    {
+        const int32_t c1 = min(k1, k0 + SPMV_CHUNK);
+        for (int32_t k = k0 + tid; k < c1; k += SPMV_ROWS) {
+            cp_async<sizeof(T)>(sval + (k - k0), a.vals + k, pol);
+            cp_async<4>(scol + (k - k0), a.colind + k, pol);
+        }
+    }
+    // the vectors written by the previous step are complete and visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     // The epilogue's row-aligned inputs do not depend on the product: load
     // them now, so their latency overlaps the staging and the gathers.
@@ -81,10 +98,11 @@ k_spmv_step(const StepArgs<T> a) {
     T acc = T(0);
     for (int32_t c0 = k0; c0 < k1; c0 += SPMV_CHUNK) {
         const int32_t c1 = min(k1, c0 + SPMV_CHUNK);
-        for (int32_t k = c0 + tid; k < c1; k += SPMV_ROWS) {
-            cp_async<sizeof(T)>(sval + (k - c0), a.vals + k, pol);
-            cp_async<4>(scol + (k - c0), a.colind + k, pol);
-        }
+        if (c0 != k0)   // the first chunk was issued before the wait
+            for (int32_t k = c0 + tid; k < c1; k += SPMV_ROWS) {
+                cp_async<sizeof(T)>(sval + (k - c0), a.vals + k, pol);
+                cp_async<4>(scol + (k - c0), a.colind + k, pol);
+            }
         cp_async_wait_all();
         __syncthreads();
         const int32_t lo = max(my_lo, c0) - c0;
@@ -202,17 +220,32 @@ template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s) {
     if (a.n <= 0) return 0;
     const int grid = spmv_grid_blocks(a.n);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(SPMV_ROWS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
     switch (op) {
-        case OP_SPMV: k_spmv_step<T, OP_SPMV><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_RESID: k_spmv_step<T, OP_RESID><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_PHI_REAL: k_spmv_step<T, OP_PHI_REAL><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_PHI_PAIR2: k_spmv_step<T, OP_PHI_PAIR2><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_P_REAL: k_spmv_step<T, OP_P_REAL><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_P_PAIR1: k_spmv_step<T, OP_P_PAIR1><<<grid, SPMV_ROWS, 0, s>>>(a); break;
-        case OP_P_PAIR2: k_spmv_step<T, OP_P_PAIR2><<<grid, SPMV_ROWS, 0, s>>>(a); break;
+        case OP_SPMV: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_SPMV>, a); break;
+        case OP_RESID: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_RESID>, a); break;
+        case OP_PHI_REAL: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_REAL>, a); break;
+        case OP_PHI_PAIR2: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_PAIR2>, a); break;
+        case OP_P_REAL: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_REAL>, a); break;
+        case OP_P_PAIR1: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR1>, a); break;
+        case OP_P_PAIR2: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR2>, a); break;
         default: return PPG_ERR_ARG;
     }
     ++g_launches;
+    if (e != cudaSuccess) {
+        set_cuda_error(e, "cudaLaunchKernelEx(k_spmv_step)");
+        return PPG_ERR_CUDA;
+    }
     int32_t rc = check_launch("k_spmv_step");
     return rc < 0 ? rc : grid;
 }
