@@ -102,6 +102,8 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     double acc[DOT_CH];
 #pragma unroll
     for (int q = 0; q < DOT_CH; ++q) acc[q] = 0.0;
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();
     const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
     int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
     for (; r + stride < n; r += 2 * stride) {   // two rows per trip: 18 loads in flight
@@ -150,6 +152,8 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     __shared__ double sh[ORTHO_MAXC];
     __shared__ double sred[ORTHO_WARPS];
     const int tid = threadIdx.x;
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();
     for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = h[c];
     __syncthreads();
     double nacc = 0.0;
@@ -187,9 +191,10 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, 
     if (ncol < 1 || ncol + 1 > ORTHO_MAXC + 2) return PPG_ERR_ARG;
     const int nvals = ncol + (with_self ? 1 : 0);
     const dim3 grid(ws.grid, (nvals + DOT_CH - 1) / DOT_CH);
-    k_mdot<<<grid, ORTHO_THREADS, 0, s>>>(V, ldv, ncol, w, n, with_self ? 1 : 0, ws.part,
-                                          ws.counter, h_out);
+    const cudaError_t e = launch_pdl(k_mdot, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
+                                     with_self ? 1 : 0, ws.part, ws.counter, h_out);
     ++g_launches;
+    if (e != cudaSuccess) { set_cuda_error(e, "launch k_mdot"); return PPG_ERR_CUDA; }
     return check_launch("k_mdot");
 }
 
@@ -198,9 +203,11 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
                           const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
     const int grid = max(1, min((n + ORTHO_THREADS - 1) / ORTHO_THREADS, 152 * 8));
-    k_gemv_sub<<<grid, ORTHO_THREADS, 0, s>>>(V, ldv, ncol, w, n, hin, with_norm ? 1 : 0,
-                                              ws.part, ws.counter + 1, nrm_out);
+    const cudaError_t e = launch_pdl(k_gemv_sub, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv,
+                                     ncol, w, n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1,
+                                     nrm_out);
     ++g_launches;
+    if (e != cudaSuccess) { set_cuda_error(e, "launch k_gemv_sub"); return PPG_ERR_CUDA; }
     return check_launch("k_gemv_sub");
 }
 
@@ -216,6 +223,8 @@ __global__ void k_finish_column(GmresState st, int ldh, int j, const double* h1,
     __shared__ double col[ORTHO_MAXC + 1];
     __shared__ double scs[ORTHO_MAXC], ssn[ORTHO_MAXC];
     const int lane = threadIdx.x;
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();
     for (int i = lane; i <= j; i += 32) col[i] = h1[i] + h2[i];
     if (givens)
         for (int i = lane; i < j; i += 32) {
@@ -272,8 +281,10 @@ int32_t launch_finish_column(const GmresState& st, int ldh, int j, const double*
                              const double* h2, const double* nrm, bool givens,
                              double bnorm, double brtol, cudaStream_t s) {
     if (j + 1 > ORTHO_MAXC) return PPG_ERR_ARG;
-    k_finish_column<<<1, 32, 0, s>>>(st, ldh, j, h1, h2, nrm, givens ? 1 : 0, bnorm, brtol);
+    const cudaError_t e = launch_pdl(k_finish_column, dim3(1), dim3(32), 0, s, st, ldh, j, h1,
+                                     h2, nrm, givens ? 1 : 0, bnorm, brtol);
     ++g_launches;
+    if (e != cudaSuccess) { set_cuda_error(e, "launch k_finish_column"); return PPG_ERR_CUDA; }
     return check_launch("k_finish_column");
 }
 
@@ -325,6 +336,8 @@ template int32_t launch_gemv_acc<float>(const float*, int64_t, int, const double
 
 // y = x * scal[2]   (x may equal y)
 __global__ void k_scale(const double* x, double* y, int32_t n, const double* sp) {
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();
     const double a = *sp;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x)
@@ -334,8 +347,9 @@ __global__ void k_scale(const double* x, double* y, int32_t n, const double* sp)
 int32_t launch_scale(const double* x, double* y, int32_t n, const double* sp,
                      cudaStream_t s) {
     const int grid = max(1, min((n + 255) / 256, 152 * 8));
-    k_scale<<<grid, 256, 0, s>>>(x, y, n, sp);
+    const cudaError_t e = launch_pdl(k_scale, dim3(grid), dim3(256), 0, s, x, y, n, sp);
     ++g_launches;
+    if (e != cudaSuccess) { set_cuda_error(e, "launch k_scale"); return PPG_ERR_CUDA; }
     return check_launch("k_scale");
 }
 

@@ -35,6 +35,30 @@ extern thread_local int64_t g_launches;   // kernels launched by this thread
 
 int32_t check_launch(const char* where);
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may
+// start while the previous kernel in the stream finishes; it must call
+// PPG_PDL_WAIT() before touching any global data that earlier work writes
+// (and before writing anything earlier work reads).  PPG_PDL_TRIGGER() lets
+// the next kernel start launching.
+#define PPG_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;")
+#define PPG_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------
 // Fused SpMV-root step (one pass over A per root; Algorithms 1 and 3)
 // ---------------------------------------------------------------------------
