@@ -232,6 +232,32 @@ int32_t ppg_solve_flex(const ppg_csr* A64, const ppg_csr* A32,
                        int32_t m, double tol, const ppg_opts* opts,
                        ppg_stats* stats, void* stream);
 
+/* Batching form: nsys independent systems A_s x = b_s with nrhs (1 or 4)
+ * right-hand sides each, solved together.  Each system gets its own
+ * polynomial from one batched GMRES(d) run (Algorithm 4 step 1; v0[s] is
+ * system s's random start vector) and is solved by flexible GMRES(m) in
+ * FP64 with z = p(A_s) v applied by Algorithm 3 in FP32 (the precision
+ * form of ppg_solve_flex).  All systems and right-hand sides advance in the
+ * same launches: the systems are packed block-diagonally (each padded to
+ * 256-row tiles), the right-hand sides interleaved, and a restart cycle of
+ * the whole batch is replayed as one CUDA graph (captured on `stream`;
+ * on the legacy default stream the cycle is launched directly).
+ *   As      host array of nsys CSR descriptors (PPG_F64, device pointers)
+ *   B, X    host arrays of nsys device pointers, each n_s * nrhs doubles,
+ *           column-major (right-hand side k at offset k * n_s)
+ *   v0      host array of nsys device pointers (n_s doubles each)
+ *   roots_out (nullable) nsys caller-owned ppg_roots receiving each
+ *           system's roots; relres_out / iters_out (nullable) host arrays
+ *           of nsys * nrhs entries (solve s * nrhs + k): final true relative
+ *           residual and Arnoldi steps.
+ * Packed sizes must stay below 2^31 entries.  Returns PPG_OK when every
+ * solve converged, PPG_NOT_CONVERGED otherwise.  Synchronises. */
+int32_t ppg_solve_batched(int32_t nsys, const ppg_csr* As, int32_t nrhs,
+                          const double* const* B, double* const* X,
+                          const double* const* v0, int32_t d, int32_t m, double tol,
+                          const ppg_opts* opts, ppg_roots* roots_out, ppg_stats* stats,
+                          double* relres_out, int32_t* iters_out, void* stream);
+
 /* Stability check StCh of Section 3.5: ||r1 - r2|| with r1 = b - A p(A) b
  * (Algorithm 3) and r2 = pi(A) b = b - phi(A) b (Algorithm 1).  A PPG_F64,
  * b device double.  Writes the host double *stch.  Synchronises. */

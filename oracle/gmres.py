@@ -283,3 +283,23 @@ def adjoint_grads(A, AT, roots, x: np.ndarray, gx: np.ndarray, m: int,
     rows = np.repeat(np.arange(rowptr.shape[0] - 1), np.diff(rowptr))
     gvals = -lam[rows] * x[colind]
     return lam, gvals, st
+
+
+def batched_solve(problems, d: int, m: int, tol: float, inner: str = "f32",
+                  max_cycles: int = 1000):
+    """The batching form, defined as what it computes: for every system
+    (A, B, v0) its own polynomial from GMRES(d) on v0, then FGMRES(m) with
+    p(A) applied in float32 for every right-hand side, independently.
+    Returns per-system (roots, [x per rhs], [stats per rhs])."""
+    from .poly import build_poly
+    out = []
+    for A, B, v0 in problems:
+        As = A.to_scipy() if hasattr(A, "to_scipy") else A
+        pp = build_poly(As, d, v0)
+        xs, sts = [], []
+        for b in B:
+            x, st = fgmres_p(As, pp.roots, b, m, tol, inner=inner, max_cycles=max_cycles)
+            xs.append(x)
+            sts.append(st)
+        out.append((pp.roots, xs, sts))
+    return out

@@ -11,7 +11,7 @@ from typing import Optional, Tuple
 import numpy as np
 import torch
 
-from ._binding import (PPG_F32, PPG_F64, PPGError, Roots, check, default_opts, lib,
+from ._binding import (PPG_F32, PPG_F64, PPGError, Roots, check, default_opts, lib, ppg_roots,
                        ppg_csr, ppg_stats, csr_validate_host, _dp)
 
 
@@ -171,6 +171,39 @@ def solve_flex(A64: CSR, A32: CSR, b: torch.Tensor, roots: Roots, m: int = 50,
     s = st.as_dict()
     s["status"] = rc
     return x, s
+
+
+def solve_batched(As, Bs, v0s, d: int = 20, m: int = 30, tol: float = 1e-10,
+                  max_cycles: int = 10000, Xs=None, stream=None):
+    """Batching form: systems As[s] (FP64 CSR) with right-hand sides Bs[s]
+    (tensor (nrhs, n_s), nrhs = 1 or 4, same nrhs for all) and start vectors
+    v0s[s]; each system gets its own polynomial; FGMRES(m) with FP32 p(A).
+    Returns (Xs, info) with info = {"roots", "relres", "iters", "stats",
+    "status"}."""
+    nsys = len(As)
+    nrhs = Bs[0].shape[0] if Bs[0].dim() == 2 else 1
+    csrs = (ppg_csr * nsys)(*[A.s for A in As])
+    if Xs is None:
+        Xs = [torch.empty_like(b) for b in Bs]
+    for t in list(Bs) + list(Xs) + list(v0s):
+        _need_cuda(t)
+    bp = (C.c_void_p * nsys)(*[b.data_ptr() for b in Bs])
+    xp = (C.c_void_p * nsys)(*[x.data_ptr() for x in Xs])
+    vp = (C.c_void_p * nsys)(*[v.data_ptr() for v in v0s])
+    roots = [Roots(4 * d + 8) for _ in range(nsys)]
+    rarr = (ppg_roots * nsys)(*[r.s for r in roots])
+    rel = np.zeros(nsys * nrhs)
+    its = np.zeros(nsys * nrhs, dtype=np.int32)
+    o = default_opts(max_cycles=max_cycles)
+    st = ppg_stats()
+    rc = lib.ppg_solve_batched(nsys, csrs, nrhs, bp, xp, vp, d, m, tol, C.byref(o), rarr,
+                               C.byref(st), _dp(rel),
+                               its.ctypes.data_as(C.POINTER(C.c_int32)), _stream(stream))
+    check(rc, "ppg_solve_batched")
+    for r, rs in zip(roots, rarr):
+        r.s.n_orig, r.s.n_added, r.s.n_total = rs.n_orig, rs.n_added, rs.n_total
+    return Xs, {"roots": roots, "relres": rel.reshape(nsys, nrhs),
+                "iters": its.reshape(nsys, nrhs), "stats": st.as_dict(), "status": rc}
 
 
 def stability_check(A: CSR, roots: Roots, b: torch.Tensor, stream=None) -> float:

@@ -165,40 +165,7 @@ template int32_t run_plan<float>(const std::vector<Step>&, const int32_t*, const
 // Workspace: one stream-ordered allocation carved into aligned pieces
 // ---------------------------------------------------------------------------
 
-struct Arena {
-    size_t bytes = 0;
-    char* base = nullptr;
-    struct Req { void** out; size_t bytes; };
-    std::vector<Req> reqs;
-    template <typename T>
-    void add(T** out, size_t count) {
-        reqs.push_back({(void**)out, count * sizeof(T)});
-    }
-    int32_t alloc(cudaStream_t s) {
-        size_t off = 0;
-        for (auto& r : reqs) off += (r.bytes + 255) / 256 * 256;
-        bytes = off;
-        if (bytes == 0) return PPG_OK;
-        cudaError_t e = cudaMallocAsync((void**)&base, bytes, s);
-        if (e != cudaSuccess) {
-            set_cuda_error(e, "cudaMallocAsync");
-            cudaGetLastError();
-            return PPG_ERR_NOMEM;
-        }
-        off = 0;
-        for (auto& r : reqs) {
-            *r.out = base + off;
-            off += (r.bytes + 255) / 256 * 256;
-        }
-        return PPG_OK;
-    }
-    void release(cudaStream_t s) {
-        if (base) cudaFreeAsync(base, s);
-        base = nullptr;
-    }
-};
-
-static int32_t setup_device_pool() {
+int32_t setup_device_pool() {
     static uint64_t done_mask = 0;
     int dev = 0;
     PPG_CUDA(cudaGetDevice(&dev));

@@ -59,6 +59,43 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// One stream-ordered scratch allocation carved into 256-byte aligned pieces.
+struct Arena {
+    size_t bytes = 0;
+    char* base = nullptr;
+    struct Req { void** out; size_t bytes; };
+    std::vector<Req> reqs;
+    template <typename T>
+    void add(T** out, size_t count) {
+        reqs.push_back({(void**)out, count * sizeof(T)});
+    }
+    int32_t alloc(cudaStream_t s) {
+        size_t off = 0;
+        for (auto& r : reqs) off += (r.bytes + 255) / 256 * 256;
+        bytes = off;
+        if (bytes == 0) return PPG_OK;
+        cudaError_t e = cudaMallocAsync((void**)&base, bytes, s);
+        if (e != cudaSuccess) {
+            set_cuda_error(e, "cudaMallocAsync");
+            cudaGetLastError();
+            return PPG_ERR_NOMEM;
+        }
+        off = 0;
+        for (auto& r : reqs) {
+            *r.out = base + off;
+            off += (r.bytes + 255) / 256 * 256;
+        }
+        return PPG_OK;
+    }
+    void release(cudaStream_t s) {
+        if (base) cudaFreeAsync(base, s);
+        base = nullptr;
+    }
+};
+
+// Keep freed scratch cached in the device's default pool (once per device).
+int32_t setup_device_pool();
+
 // ---------------------------------------------------------------------------
 // Fused SpMV-root step (one pass over A per root; Algorithms 1 and 3)
 // ---------------------------------------------------------------------------

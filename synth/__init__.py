@@ -29,7 +29,7 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 __all__ = [
-    "CSRHost", "cd2d", "cd3d", "diag_csr", "smooth_field", "streams",
+    "CSRHost", "cd2d", "cd3d", "diag_csr", "smooth_field", "streams", "batch_problem",
     "ProblemSpec", "problem", "PROBLEMS", "batch_specs", "uniform_rhs",
     "gaussian_v0", "ex7_diagonal", "ex11_diagonal",
 ]
@@ -256,4 +256,19 @@ def problem(name: str, scale: Optional[int] = None) -> ProblemSpec:
     raise KeyError(name)
 
 
-PROBLEMS = ("cd2d_50", "cd2d_1000", "cd3d_160", "cd2d_field_512")
+def batch_problem(nsys: int = 64, seed: int = 104, side_lo: int = 64, side_hi: int = 512,
+                  nrhs: int = 4, bh_lo: float = 0.1, bh_hi: float = 2.0):
+    """Batch of independent 2-D convection-diffusion systems (the batching
+    workload): grid sides ~ U{side_lo..side_hi}, beta*h ~ U[bh_lo, bh_hi],
+    nrhs right-hand sides ~ U[-1, 1] and one Gaussian v0 per system.
+    Returns a list of (A, B (nrhs x n), v0)."""
+    rv, rb, _, rbatch = streams(seed)
+    out = []
+    for side, bh in batch_specs(rbatch, nsys, side_lo, side_hi, bh_lo, bh_hi):
+        A = cd2d(side, bh)
+        B = np.stack([uniform_rhs(rb, A.n) for _ in range(nrhs)])
+        out.append((A, B, gaussian_v0(rv, A.n)))
+    return out
+
+
+PROBLEMS = ("cd2d_50", "cd2d_1000", "cd3d_160", "cd2d_field_512", "batch_64x4")
