@@ -366,6 +366,8 @@ def run_ours(args, rank, local, world):
         "clocks": clk,
         "plain_gmres50": plain,
     }
+    if rank == 0 and not args.no_forms:
+        line["forms"] = measure_forms(device)
     if rank == 0 and not args.no_cpu_baseline:
         s = _run_oracle_subprocess(args.oracle_iters)
         v = _extrapolate(s, st["iters"], st["cycles"])
@@ -385,6 +387,107 @@ def run_ours(args, rank, local, world):
 
 def st_degree(stats, R):
     return int(R.n_total)
+
+
+def _timed(torch, fn):
+    """Run fn() once between CUDA events on the current stream: (result, ms)."""
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def measure_forms(device):
+    """The three forms beside the plain FP64 method, each against the plain
+    FP64 PP-GMRES on the same GPU at relative residual 1e-10 (one run each,
+    after one warm-up run)."""
+    import numpy as np
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+    import synth
+
+    out = {}
+    # precision form: 3-D 160^3, FP32 p(A) inside FP64 FGMRES(50) vs full FP64
+    P = synth.problem("cd3d_160")
+    A64 = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
+    A32 = A64.astype(torch.float32)
+    b = torch.from_numpy(P.b).to(device)
+    v0 = torch.from_numpy(P.v0).to(device)
+    R, t_build = _timed(torch, lambda: ppg.build_poly(A64, P.d, v0))
+    ppg.solve_flex(A64, A32, b, R, P.m, P.tol)
+    (x32, s32), t32 = _timed(torch, lambda: ppg.solve_flex(A64, A32, b, R, P.m, P.tol))
+    ppg.solve(A64, b, P.m, P.tol, roots=R)
+    (x64, s64), t64 = _timed(torch, lambda: ppg.solve(A64, b, P.m, P.tol, roots=R))
+    As = P.A.to_scipy()
+    xh32, xh64 = x32.cpu().numpy(), x64.cpu().numpy()
+    out["precision_cd3d_160"] = {
+        "n": P.A.n, "degree": R.n_total, "build_ms": round(t_build, 2),
+        "fp32_inner_ms": round(t32, 2), "fp32_inner_iters": s32["iters"],
+        "fp32_inner_relres": float(np.linalg.norm(P.b - As @ xh32) / np.linalg.norm(P.b)),
+        "fp64_ms": round(t64, 2), "fp64_iters": s64["iters"],
+        "fp64_relres": float(np.linalg.norm(P.b - As @ xh64) / np.linalg.norm(P.b)),
+        "rel_diff_fp32_vs_fp64": float(np.linalg.norm(xh32 - xh64) / np.linalg.norm(xh64)),
+    }
+    del A64, A32, x32, x64
+    # batching form: 64 systems x 4 right-hand sides in one call
+    probs = synth.batch_problem(nsys=64, seed=104)
+    dA = [ppg.CSR.from_host(A.rowptr, A.colind, A.vals, device=device) for A, _, _ in probs]
+    dB = [torch.from_numpy(np.ascontiguousarray(B)).to(device) for _, B, _ in probs]
+    dv = [torch.from_numpy(v).to(device) for _, _, v in probs]
+    side = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(side):
+        ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10)
+        (Xs, info), tb = _timed(torch, lambda: ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10))
+    worst = max(float(np.linalg.norm(B[k] - A.to_scipy() @ Xs[s][k].cpu().numpy())
+                      / np.linalg.norm(B[k]))
+                for s, (A, B, _) in enumerate(probs) for k in range(4))
+    # the plain FP64 method one solve at a time on 8 sampled systems
+    sample = list(range(0, 64, 8))
+    seq_ms = 0.0
+    for s in sample:
+        def one():
+            Rs = ppg.build_poly(dA[s], 20, dv[s])
+            for k in range(4):
+                ppg.solve(dA[s], dB[s][k].contiguous(), 30, 1e-10, roots=Rs)
+        _, t = _timed(torch, one)
+        seq_ms += t
+    out["batched_64x4"] = {
+        "solves": 256, "total_rows": int(sum(A.n for A, _, _ in probs)),
+        "batched_ms": round(tb, 2), "worst_true_relres": worst,
+        "cycles": info["stats"]["cycles"], "total_iters": info["stats"]["iters"],
+        "fp64_sequential_ms_extrapolated": round(seq_ms / len(sample) * 64, 1),
+        "fp64_sequential_sample": "8 of 64 systems (every 8th), 4 rhs each, one at a time",
+    }
+    del dA, dB, dv, Xs
+    # differentiation form: 512^2 with a per-node convection field
+    P = synth.problem("cd2d_field_512")
+    A = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
+    R = ppg.build_poly(A, P.d, torch.from_numpy(P.v0).to(device))
+    xstar = torch.from_numpy(P.extra["xstar"]).to(device)
+
+    def fwd():
+        bt = torch.from_numpy(P.b).to(device).requires_grad_(True)
+        vt = A.vals.clone().requires_grad_(True)
+        x = ppg.PPGMRESFunction.apply(bt, vt, A, R, P.m, P.tol, None, 500)
+        return bt, vt, x
+    fwd()
+    (bt, vt, x), tf = _timed(torch, fwd)
+    loss = 0.5 * torch.sum((x - xstar) ** 2)
+    _, tbk = _timed(torch, lambda: loss.backward())
+    _, tplain = _timed(torch, lambda: ppg.solve(A, torch.from_numpy(P.b).to(device), P.m, P.tol,
+                                                 roots=R))
+    out["adjoint_cd2d_field_512"] = {
+        "n": P.A.n, "forward_ms": round(tf, 2), "backward_ms": round(tbk, 2),
+        "fp64_forward_solve_ms": round(tplain, 2),
+        "grad_b_norm": float(torch.linalg.norm(bt.grad).item()),
+    }
+    return out
 
 
 PROFILE_ROOTS = (7.5, 0.35, 3.9, 6.1, 1.6, 4.9)   # real roots spread over the spectrum
@@ -449,6 +552,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--plain-cycles", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--oracle-iters", type=int, default=2)
     ap.add_argument("--ref-iters", type=int, default=200)
     ap.add_argument("--ref-cycles", type=int, default=4)

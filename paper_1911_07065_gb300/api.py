@@ -253,10 +253,12 @@ class PPGMRESFunction(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, b, vals, A: CSR, roots: Roots, m: int, tol: float, AT: Optional[CSR]):
+    def forward(ctx, b, vals, A: CSR, roots: Roots, m: int, tol: float, AT: Optional[CSR],
+                max_cycles: int = 10000):
         Aw = A.with_vals(vals.detach().contiguous())
-        x, st = solve(Aw, b.detach().contiguous(), m, tol, roots=roots)
+        x, st = solve(Aw, b.detach().contiguous(), m, tol, roots=roots, max_cycles=max_cycles)
         ctx.A, ctx.roots, ctx.m, ctx.tol, ctx.AT = Aw, roots, m, tol, AT
+        ctx.max_cycles = max_cycles
         ctx.save_for_backward(x)
         ctx.stats = st
         return x
@@ -267,6 +269,7 @@ class PPGMRESFunction(torch.autograd.Function):
         AT = ctx.AT
         if AT is None:
             AT = ctx.A.transpose()
-        lam, _ = solve(AT, gx.contiguous(), ctx.m, ctx.tol, roots=ctx.roots)
+        lam, _ = solve(AT, gx.contiguous(), ctx.m, ctx.tol, roots=ctx.roots,
+                       max_cycles=ctx.max_cycles)
         gvals = adjoint_vals_grad(ctx.A, lam, x)
-        return lam, gvals, None, None, None, None, None
+        return lam, gvals, None, None, None, None, None, None
