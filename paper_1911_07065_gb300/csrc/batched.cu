@@ -22,7 +22,9 @@
 // (deterministic); one thread per solve applies the Givens rotations and
 // decides on the device whether its solve stops in this cycle, so a whole
 // restart cycle needs no host synchronisation and is captured once as a
-// CUDA graph and replayed for every cycle.
+// CUDA graph and replayed for every cycle.  CTAs of a system whose solves
+// have all stopped return at once, so converged systems cost next to
+// nothing in later steps and cycles.
 //
 // Tiling.  The rows per CTA of the FP32 root-step kernel (64, 128 or 256)
 // are chosen by timing the candidates on the batch at set-up.
@@ -75,9 +77,13 @@ __device__ __forceinline__ void ld_rhs(const T* p, T (&out)[NR]) {
     }
 }
 
-template <typename T, int NR>
-__device__ __forceinline__ T coef(double c) {
-    return (T)c;
+// does any right-hand side of system s still take steps in this cycle?
+template <int NR>
+__device__ __forceinline__ bool sys_live(const int32_t* active, int s) {
+    int any = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) any |= active[s * NR + k];
+    return any != 0;
 }
 
 // One pass of the batch: step steps[s] of every system s, applied to the
@@ -88,7 +94,8 @@ template <typename T, int NR>
 __global__ void __launch_bounds__(256)
 k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
         const T* __restrict__ vals, const BStep* __restrict__ steps,
-        const int32_t* __restrict__ sys_of_tile, BufSet<T> b, double* part) {
+        const int32_t* __restrict__ sys_of_tile, BufSet<T> b, double* part,
+        const int32_t* __restrict__ active) {
     __shared__ T sval[BCHUNK];
     __shared__ int32_t scol[BCHUNK];
     __shared__ int32_t srp[BT + 1];
@@ -99,6 +106,7 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
     const int s = sys_of_tile[row0 / BT];
     const BStep st = steps[s];
     if (st.op == OP_NOP) return;   // uniform over the CTA
+    if (active && !sys_live<NR>(active, s)) return;   // every solve of s has stopped
     for (int i = tid; i <= rows; i += rows) srp[i] = __ldg(rowptr + row0 + i);
     __syncthreads();
     const int32_t k0 = srp[0], k1 = srp[rows];
@@ -198,8 +206,11 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
 template <int NR>
 __global__ void __launch_bounds__(256)
 k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __restrict__ w,
-       int with_self, double* part, int64_t pstr) {
+       int with_self, double* part, int64_t pstr, const int32_t* __restrict__ sys_of_tile,
+       const int32_t* __restrict__ active) {
     __shared__ double sred[8][BCH][NR];
+    // stopped systems: their partial sums are never read
+    if (active && !sys_live<NR>(active, sys_of_tile[blockIdx.x])) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = tid % NR;
     constexpr int RP = 256 / NR;   // rows per pass
@@ -266,7 +277,7 @@ template <int NR>
 __global__ void __launch_bounds__(256)
 k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
        const double* __restrict__ h, int nsolve, const int32_t* __restrict__ sys_of_tile,
-       int with_norm, double* part) {
+       int with_norm, double* part, const int32_t* __restrict__ active) {
     __shared__ double sh[ORTHO_MAXC][NR];
     __shared__ double sred[8][NR];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -274,6 +285,7 @@ k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
     constexpr int RP = 256 / NR;
     const int64_t tile = blockIdx.x;
     const int s = sys_of_tile[tile];
+    if (active && !sys_live<NR>(active, s)) return;
     for (int e = tid; e < ncol * NR; e += 256)
         sh[e / NR][e % NR] = h[(size_t)(e / NR) * nsolve + s * NR + e % NR];
     __syncthreads();
@@ -533,18 +545,18 @@ std::map<std::tuple<int64_t, int64_t, int>, int> g_tune;
 
 template <int NR>
 int32_t launch_bstep_f(const Batch& B, const BStep* steps, const BufSet<float>& bs, int rpc,
-                       cudaStream_t s) {
+                       cudaStream_t s, const int32_t* active = nullptr) {
     k_bstep<float, NR><<<(unsigned)(B.N / rpc), rpc, 0, s>>>(B.rowptr, B.colind, B.v32, steps,
-                                                             B.sys_of_tile, bs, nullptr);
+                                                             B.sys_of_tile, bs, nullptr, active);
     BCHECK("k_bstep<float>");
     return PPG_OK;
 }
 
 template <int NR>
 int32_t launch_bstep_d(const Batch& B, const BStep* steps, const BufSet<double>& bs,
-                       double* part, cudaStream_t s) {
+                       double* part, cudaStream_t s, const int32_t* active = nullptr) {
     k_bstep<double, NR><<<(unsigned)(B.N / 256), 256, 0, s>>>(B.rowptr, B.colind, B.v64, steps,
-                                                              B.sys_of_tile, bs, part);
+                                                              B.sys_of_tile, bs, part, active);
     BCHECK("k_bstep<double>");
     return PPG_OK;
 }
@@ -568,7 +580,7 @@ struct Work {
 
 template <int NR>
 int32_t cgs2_batch(const Batch& B, Work& W, int j, double* wcol, int with_self, int64_t ldV,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int32_t* active = nullptr) {
     const int nsolve = B.nsys * NR;
     const int ncol = j + 1;
     const int64_t pstr = W.pstr;
@@ -577,13 +589,13 @@ int32_t cgs2_batch(const Batch& B, Work& W, int j, double* wcol, int with_self, 
         const int nvals = ncol + self;
         double* h = pass == 0 ? W.h1 : W.h2;
         k_bdot<NR><<<dim3((unsigned)B.ntiles, (nvals + BCH - 1) / BCH), 256, 0, s>>>(
-            W.V, ldV, ncol, wcol, self, W.part, pstr);
+            W.V, ldV, ncol, wcol, self, W.part, pstr, B.sys_of_tile, active);
         BCHECK("k_bdot");
         k_bsegsum<<<dim3(B.nsys, (nvals + 7) / 8), 256, 0, s>>>(W.part, pstr, nvals, NR, B.tile0,
                                                                 B.nsys, h);
         BCHECK("k_bsegsum");
         k_bsub<NR><<<(unsigned)B.ntiles, 256, 0, s>>>(W.V, ldV, ncol, wcol, h, nsolve,
-                                                      B.sys_of_tile, pass == 1, W.part);
+                                                      B.sys_of_tile, pass == 1, W.part, active);
         BCHECK("k_bsub");
     }
     k_bsegsum<<<dim3(B.nsys, 1), 256, 0, s>>>(W.part, NR, 1, NR, B.tile0, B.nsys, W.nrm);
@@ -655,14 +667,15 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
         fs.p[B_B] = W.fb;
         fs.p[B_C] = W.fc;
         for (int k = 0; k < K; ++k)
-            PPG_TRY(launch_bstep_f<NR>(B, W.steps_p + (size_t)k * B.nsys, fs, B.rows_per_cta, s));
+            PPG_TRY(launch_bstep_f<NR>(B, W.steps_p + (size_t)k * B.nsys, fs, B.rows_per_cta, s,
+                                       W.st.active));
         k_cast32<<<elem_grid(total), 256, 0, s>>>(zj, W.zd, total);
         BCHECK("k_cast32");
         BufSet<double> ds{};
         ds.p[B_IN] = W.zd;
         ds.p[B_OUT] = w;
-        PPG_TRY(launch_bstep_d<NR>(B, W.steps_spmv, ds, nullptr, s));
-        PPG_TRY(cgs2_batch<NR>(B, W, j, w, 0, ldV, s));
+        PPG_TRY(launch_bstep_d<NR>(B, W.steps_spmv, ds, nullptr, s, W.st.active));
+        PPG_TRY(cgs2_batch<NR>(B, W, j, w, 0, ldV, s, W.st.active));
         k_bgivens<<<sg, 128, 0, s>>>(W.st, nsolve, B.ldh, B.m, j, W.h1, W.h2, W.nrm, 0, tol);
         BCHECK("k_bgivens");
         k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(w, W.st.inv, B.sys_of_tile, total);
@@ -791,6 +804,10 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
         const int32_t last = (int32_t)nnz;
         PPG_CUDA(cudaMemcpyAsync(B.rowptr + N, &last, sizeof(int32_t), cudaMemcpyHostToDevice, s));
     }
+    // stopped systems skip their rows, so basis columns they never write
+    // must hold finite values: start from zeros
+    PPG_CUDA(cudaMemsetAsync(W.V, 0, sizeof(double) * (size_t)(mk + 1) * ldV, s));
+    PPG_CUDA(cudaMemsetAsync(W.Z, 0, sizeof(float) * (size_t)m * ldV, s));
     PPG_CUDA(cudaMemsetAsync(W.st.R, 0, sizeof(double) * nsolve * B.ldh * mk, s));
     PPG_CUDA(cudaMemsetAsync(W.st.Hraw, 0, sizeof(double) * nsys * B.ldh * mk, s));
     PPG_CUDA(cudaMemsetAsync(W.st.iters, 0, sizeof(int32_t) * nsolve, s));
@@ -807,7 +824,8 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
             BCHECK("k_pack_vec");
         }
         // ||v0|| per system, V_0 = v0 / ||v0||
-        k_bdot<1><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, N, 0, W.V, 1, W.part, W.pstr);
+        k_bdot<1><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, N, 0, W.V, 1, W.part, W.pstr,
+                                                               B.sys_of_tile, nullptr);
         BCHECK("k_bdot");
         k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, 1, B.tile0, nsys, W.nrm);
         BCHECK("k_bsegsum");
@@ -910,7 +928,8 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     }
     PPG_CUDA(cudaMemsetAsync(W.X, 0, sizeof(double) * ldV, s));
     PPG_CUDA(cudaMemcpyAsync(W.V, W.Bp, sizeof(double) * ldV, cudaMemcpyDeviceToDevice, s));
-    k_bdot<NR><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, ldV, 0, W.V, 1, W.part, W.pstr);
+    k_bdot<NR><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, ldV, 0, W.V, 1, W.part, W.pstr,
+                                                           B.sys_of_tile, nullptr);
     BCHECK("k_bdot");
     k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, NR, B.tile0, nsys, W.nrm);
     BCHECK("k_bsegsum");
