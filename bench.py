@@ -74,7 +74,7 @@ def _ncu_traffic():
     if vals.get("kernel_source_hash") != _kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch_phi_real"])
+        return float(vals["dram_bytes_per_launch"])
     except Exception:
         return None
 
