@@ -199,6 +199,19 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
     }
 }
 
+template <int NR, int NQ>
+__device__ __forceinline__ void bdot_rows(const double* const* col, const double* __restrict__ w,
+                                          int64_t base, int tid, int k, double* acc) {
+    constexpr int RP = 256 / NR;   // rows per pass
+#pragma unroll
+    for (int p = 0; p < NR; ++p) {
+        const int64_t idx = (base + p * RP + tid / NR) * NR + k;
+        const double wv = w[idx];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + idx), wv, acc[q]);
+    }
+}
+
 // Partial dot products per tile: part[tile * pstr + c * NR + k] =
 // sum over the tile's rows of col_c[r, k] * w[r, k], where col_c is basis
 // column c (c < ncol) or w itself (c == ncol, with_self).  Thread t takes
@@ -216,23 +229,26 @@ k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __rest
     constexpr int RP = 256 / NR;   // rows per pass
     const int c0 = blockIdx.y * BCH;
     const int nvals = ncol + (with_self ? 1 : 0);
+    const int nq = min(BCH, nvals - c0);
     const double* col[BCH];
 #pragma unroll
     for (int q = 0; q < BCH; ++q) {
         const int c = c0 + q;
-        col[q] = (c < ncol) ? V + c * ldV : ((c == ncol && with_self) ? w : nullptr);
+        col[q] = (c < ncol) ? V + c * ldV : w;
     }
     double acc[BCH];
 #pragma unroll
     for (int q = 0; q < BCH; ++q) acc[q] = 0.0;
     const int64_t base = (int64_t)blockIdx.x * BT;
-#pragma unroll
-    for (int p = 0; p < NR; ++p) {
-        const int64_t idx = (base + p * RP + tid / NR) * NR + k;
-        const double wv = w[idx];
-#pragma unroll
-        for (int q = 0; q < BCH; ++q)
-            if (col[q]) acc[q] = fma(__ldcs(col[q] + idx), wv, acc[q]);
+    switch (nq) {   // compile-time widths: no FP64 FMA for a missing column
+        case 8: bdot_rows<NR, 8>(col, w, base, tid, k, acc); break;
+        case 7: bdot_rows<NR, 7>(col, w, base, tid, k, acc); break;
+        case 6: bdot_rows<NR, 6>(col, w, base, tid, k, acc); break;
+        case 5: bdot_rows<NR, 5>(col, w, base, tid, k, acc); break;
+        case 4: bdot_rows<NR, 4>(col, w, base, tid, k, acc); break;
+        case 3: bdot_rows<NR, 3>(col, w, base, tid, k, acc); break;
+        case 2: bdot_rows<NR, 2>(col, w, base, tid, k, acc); break;
+        default: bdot_rows<NR, 1>(col, w, base, tid, k, acc); break;
     }
     // sum over the lanes that share k
 #pragma unroll

@@ -83,6 +83,28 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter) {
     return am_last;
 }
 
+// acc[q] += sum over this thread's rows of col[q][r] w[r], q < NQ: two rows
+// per trip, so 2 (NQ + 1) loads are in flight.  NQ is a compile-time width:
+// a predicated-off FP64 FMA still occupies the FP64 pipe on GB300, so the
+// last, narrower chunk of columns must not issue FMAs for missing columns.
+template <int NQ>
+__device__ __forceinline__ void dot_rows(const double* const* col, const double* __restrict__ w,
+                                         int64_t r, int64_t stride, int64_t n, double* acc) {
+    for (; r + stride < n; r += 2 * stride) {
+        const double w0 = w[r], w1 = w[r + stride];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double a0 = __ldcs(col[q] + r), a1 = __ldcs(col[q] + r + stride);
+            acc[q] = fma(a1, w1, fma(a0, w0, acc[q]));
+        }
+    }
+    if (r < n) {
+        const double w0 = w[r];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + r), w0, acc[q]);
+    }
+}
+
 // hout[c] = sum_r V[c][r] w[r] for c < ncol, and hout[ncol] = w.w when
 // with_self.  Grid: x = row blocks (grid-stride), y = chunks of eight
 // columns, so every column chunk streams in parallel.
@@ -93,11 +115,12 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nvals = ncol + (with_self ? 1 : 0);
     const int c0 = blockIdx.y * DOT_CH;
+    const int nq = min(DOT_CH, nvals - c0);
     const double* col[DOT_CH];
 #pragma unroll
     for (int q = 0; q < DOT_CH; ++q) {
         const int c = c0 + q;
-        col[q] = (c < ncol) ? V + c * ldv : ((c == ncol && with_self) ? w : nullptr);
+        col[q] = (c < ncol) ? V + c * ldv : w;
     }
     double acc[DOT_CH];
 #pragma unroll
@@ -105,22 +128,16 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     PPG_PDL_TRIGGER();
     PPG_PDL_WAIT();
     const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
-    int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
-    for (; r + stride < n; r += 2 * stride) {   // two rows per trip: 18 loads in flight
-        const double w0 = w[r], w1 = w[r + stride];
-#pragma unroll
-        for (int q = 0; q < DOT_CH; ++q) {
-            if (col[q]) {
-                const double a0 = __ldcs(col[q] + r), a1 = __ldcs(col[q] + r + stride);
-                acc[q] = fma(a1, w1, fma(a0, w0, acc[q]));
-            }
-        }
-    }
-    if (r < n) {
-        const double w0 = w[r];
-#pragma unroll
-        for (int q = 0; q < DOT_CH; ++q)
-            if (col[q]) acc[q] = fma(__ldcs(col[q] + r), w0, acc[q]);
+    const int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
+    switch (nq) {
+        case 8: dot_rows<8>(col, w, r, stride, n, acc); break;
+        case 7: dot_rows<7>(col, w, r, stride, n, acc); break;
+        case 6: dot_rows<6>(col, w, r, stride, n, acc); break;
+        case 5: dot_rows<5>(col, w, r, stride, n, acc); break;
+        case 4: dot_rows<4>(col, w, r, stride, n, acc); break;
+        case 3: dot_rows<3>(col, w, r, stride, n, acc); break;
+        case 2: dot_rows<2>(col, w, r, stride, n, acc); break;
+        default: dot_rows<1>(col, w, r, stride, n, acc); break;
     }
     warp_reduce8(acc, lane);
     if ((lane & 3) == 0) sred[warp][lane >> 2] = acc[0];
