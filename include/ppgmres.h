@@ -232,6 +232,36 @@ int32_t ppg_solve_flex(const ppg_csr* A64, const ppg_csr* A32,
                        int32_t m, double tol, const ppg_opts* opts,
                        ppg_stats* stats, void* stream);
 
+/* Polynomial construction on a composite operator (Section 6): one cycle of
+ * GMRES(d) with the operator phi_inner(A) (phi_inner applied by Algorithm 1
+ * with the roots `inner`) from v0, harmonic Ritz values, Leja order and
+ * root adding: the roots of the outer polynomial phi_2 in double
+ * polynomial preconditioning.  inner == NULL gives ppg_build_poly.
+ * Synchronises. */
+int32_t ppg_build_poly_composite(const ppg_csr* A, const ppg_roots* inner, int32_t d,
+                                 const double* v0, const ppg_opts* opts, ppg_roots* out,
+                                 double* Hbar_host, void* stream);
+
+/* Double polynomial preconditioning (Section 6): restarted GMRES(m) on
+ * phi_2(phi_1(A)) z = b with phi_1 from r1 and phi_2 from r2 (built by
+ * ppg_build_poly_composite), x = p_1(A) p_2(phi_1(A)) z.  Each restart
+ * starts from the true residual b - phi_1(A) x' of the accumulated
+ * x' = p_2(phi_1(A)) z; the returned x is p_1(A) x'.  stats.mvps counts every
+ * SpMV (d_1 per product with phi_1(A)).  x0_given is not supported.
+ * Synchronises. */
+int32_t ppg_solve_double(const ppg_csr* A, const ppg_roots* r1, const ppg_roots* r2,
+                         const double* b, double* x, int32_t m, double tol,
+                         const ppg_opts* opts, ppg_stats* stats, void* stream);
+
+/* PP-GMRES with the polynomial changed at every restart (Section 5.2): at the
+ * start of each cycle a degree-d polynomial is built by GMRES(d) from the
+ * current residual (the first cycle from b), then one GMRES(m) cycle runs on
+ * phi(A) and x += p(A) y.  stats.mvps includes the d SpMVs of every
+ * construction.  x0_given is not supported.  Synchronises. */
+int32_t ppg_solve_chpoly(const ppg_csr* A, int32_t d, const double* b, double* x,
+                         int32_t m, double tol, const ppg_opts* opts, ppg_stats* stats,
+                         void* stream);
+
 /* Batching form: nsys independent systems A_s x = b_s with nrhs (1 or 4)
  * right-hand sides each, solved together.  Each system gets its own
  * polynomial from one batched GMRES(d) run (Algorithm 4 step 1; v0[s] is

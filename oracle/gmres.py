@@ -303,3 +303,63 @@ def batched_solve(problems, d: int, m: int, tol: float, inner: str = "f32",
             sts.append(st)
         out.append((pp.roots, xs, sts))
     return out
+
+
+class Composite:
+    """The operator M = phi_1(A) (Algorithm 1 with the inner roots), usable
+    wherever the oracle takes a matrix (``M @ v``): Arnoldi on M gives the
+    outer polynomial of double polynomial preconditioning (Section 6)."""
+
+    def __init__(self, A, roots1):
+        self.A = A
+        self.roots1 = roots1
+        self.shape = A.shape
+
+    def __matmul__(self, v):
+        return apply_phi(self.A, self.roots1, v)
+
+
+def double_pp_gmres(A, roots1: np.ndarray, roots2: np.ndarray, b: np.ndarray, m: int,
+                    tol: float, max_cycles: int = 1000):
+    """Section 6: GMRES on phi_2(phi_1(A)) z = b, x = p_1(A) p_2(phi_1(A)) z.
+    Restarts from the true residual of x' = p_2(M) z for M = phi_1(A), then
+    x = p_1(A) x' (A x = A p_1(A) x' = M x')."""
+    M = Composite(A, roots1)
+    xp, st = pp_gmres(M, roots2, b, m, tol, max_cycles=max_cycles)
+    x = apply_p(A, roots1, xp)
+    return x, st
+
+
+def chpoly_gmres(A, d: int, b: np.ndarray, m: int, tol: float, max_cycles: int = 1000):
+    """Section 5.2: PP-GMRES(m) with the polynomial rebuilt at the start of
+    every cycle by GMRES(d) from the current residual."""
+    from .poly import build_poly
+    st = SolveStats()
+    bnorm = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    beta = bnorm
+    st.true_relres = 1.0
+    for _ in range(max_cycles):
+        st.cycles += 1
+        roots = build_poly(A, d, r).roots
+        st.mvps += d
+        nd = roots.shape[0]
+
+        def op(v):
+            st.mvps += nd
+            return apply_phi(A, roots, v)
+        V, y, k = _cycle(op, r, beta, m, bnorm, tol, "cgs2", st)
+        x = x + apply_p(A, roots, V @ y)
+        st.mvps += nd - 1
+        r = b - A @ x
+        st.mvps += 1
+        beta = np.linalg.norm(r)
+        st.true_relres = beta / bnorm
+        st.true_history.append(st.true_relres)
+        if st.true_relres <= tol:
+            st.converged = True
+            break
+        if not np.isfinite(beta):
+            break
+    return x, st

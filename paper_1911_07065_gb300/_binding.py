@@ -95,6 +95,14 @@ def _load():
                                    C.POINTER(ppg_opts), C.POINTER(ppg_stats), c_vp]),
         "ppg_stability_check": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp,
                                         P_F64, c_vp]),
+        "ppg_build_poly_composite": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_i32,
+                                             c_vp, C.POINTER(ppg_opts), C.POINTER(ppg_roots),
+                                             P_F64, c_vp]),
+        "ppg_solve_double": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots),
+                                     C.POINTER(ppg_roots), c_vp, c_vp, c_i32, c_f64,
+                                     C.POINTER(ppg_opts), C.POINTER(ppg_stats), c_vp]),
+        "ppg_solve_chpoly": (c_i32, [C.POINTER(ppg_csr), c_i32, c_vp, c_vp, c_i32, c_f64,
+                                     C.POINTER(ppg_opts), C.POINTER(ppg_stats), c_vp]),
         "ppg_solve_batched": (c_i32, [c_i32, C.POINTER(ppg_csr), c_i32, C.POINTER(c_vp),
                                       C.POINTER(c_vp), C.POINTER(c_vp), c_i32, c_i32, c_f64,
                                       C.POINTER(ppg_opts), C.POINTER(ppg_roots),
@@ -119,7 +127,7 @@ EXPORTS = (
     "ppg_csr_validate_host", "ppg_build_poly", "ppg_apply_poly", "ppg_apply_phi",
     "ppg_spmv", "ppg_solve", "ppg_solve_flex", "ppg_stability_check",
     "ppg_csr_transpose", "ppg_adjoint_vals_grad", "ppg_apply_poly_noalloc",
-    "ppg_solve_batched",
+    "ppg_solve_batched", "ppg_build_poly_composite", "ppg_solve_double", "ppg_solve_chpoly",
 )
 
 

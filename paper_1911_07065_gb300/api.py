@@ -173,6 +173,54 @@ def solve_flex(A64: CSR, A32: CSR, b: torch.Tensor, roots: Roots, m: int = 50,
     return x, s
 
 
+def build_poly_composite(A: CSR, inner: Roots, d: int, v0: torch.Tensor,
+                         stability_control: bool = True, capacity: Optional[int] = None,
+                         stream=None) -> Roots:
+    """Roots of phi_2 from GMRES(d) on phi_inner(A) (Section 6)."""
+    _need_cuda(v0)
+    cap = capacity or max(16, 4 * d)
+    r = Roots(cap)
+    o = default_opts(stability_control=int(bool(stability_control)))
+    rc = lib.ppg_build_poly_composite(A.ref(), inner.ref(), d, _ptr(v0), C.byref(o), r.ref(),
+                                      None, _stream(stream))
+    if rc == -6 and capacity is None:
+        return build_poly_composite(A, inner, d, v0, stability_control, r.s.n_total + 8, stream)
+    check(rc, "ppg_build_poly_composite")
+    return r
+
+
+def solve_double(A: CSR, b: torch.Tensor, r1: Roots, r2: Roots, m: int = 50,
+                 tol: float = 1e-10, max_cycles: int = 10000, out=None, stream=None):
+    """Double polynomial preconditioning: GMRES(m) on phi_2(phi_1(A)) z = b,
+    x = p_1(A) p_2(phi_1(A)) z.  Returns (x, stats)."""
+    _need_cuda(b)
+    x = torch.empty_like(b) if out is None else out
+    o = default_opts(max_cycles=max_cycles)
+    st = ppg_stats()
+    rc = lib.ppg_solve_double(A.ref(), r1.ref(), r2.ref(), _ptr(b), _ptr(x), m, tol,
+                              C.byref(o), C.byref(st), _stream(stream))
+    check(rc, "ppg_solve_double")
+    s = st.as_dict()
+    s["status"] = rc
+    return x, s
+
+
+def solve_chpoly(A: CSR, b: torch.Tensor, d: int, m: int = 50, tol: float = 1e-10,
+                 max_cycles: int = 10000, out=None, stream=None):
+    """PP-GMRES with the degree-d polynomial rebuilt from the residual at
+    every restart (Section 5.2).  Returns (x, stats)."""
+    _need_cuda(b)
+    x = torch.empty_like(b) if out is None else out
+    o = default_opts(max_cycles=max_cycles)
+    st = ppg_stats()
+    rc = lib.ppg_solve_chpoly(A.ref(), d, _ptr(b), _ptr(x), m, tol, C.byref(o), C.byref(st),
+                              _stream(stream))
+    check(rc, "ppg_solve_chpoly")
+    s = st.as_dict()
+    s["status"] = rc
+    return x, s
+
+
 def solve_batched(As, Bs, v0s, d: int = 20, m: int = 30, tol: float = 1e-10,
                   max_cycles: int = 10000, Xs=None, stream=None):
     """Batching form: systems As[s] (FP64 CSR) with right-hand sides Bs[s]

@@ -288,6 +288,91 @@ static int32_t cgs2_column(SolveCore& c, int j, double* w, bool with_self, Event
     return PPG_OK;
 }
 
+// Algorithm 4 step 1 with operator M = A, or M = phi_inner(A) when inner is
+// given (the second polynomial of double polynomial preconditioning,
+// Section 6): d Arnoldi steps with CGS2 from v0, then the host steps.
+static int32_t build_core(const ppg_csr* A, int d, const double* v0, const ppg_opts& o,
+                          const ppg_roots* inner, ppg_roots* out, double* Hbar_host,
+                          cudaStream_t s) {
+    PPG_TRY(setup_device_pool());
+    const int32_t n = A->n;
+    const int ldh = d + 1;
+    SolveCore c{};
+    c.A64 = A;
+    c.s = s;
+    c.ldv = pad_ld(n);
+    Arena ar;
+    ar.add(&c.V, (size_t)c.ldv * (d + 1));
+    const int sg = spmv_grid_blocks(n);
+    ar.add(&c.spart, (size_t)sg + 1024);
+    c.ows.grid = ortho_grid(n);
+    ar.add(&c.ows.part, ortho_part_doubles(c.ows.grid));
+    ar.add(&c.ows.counter, 4);
+    ar.add(&c.ows.h1, ORTHO_MAXC + 2);
+    ar.add(&c.ows.h2, ORTHO_MAXC + 2);
+    ar.add(&c.ows.nrm, 4);
+    ar.add(&c.gs.Hraw, (size_t)ldh * d);
+    ar.add(&c.gs.scal, 8);
+    if (inner) {
+        ar.add(&c.va, (size_t)n);
+        ar.add(&c.vb, (size_t)n);
+        ar.add(&c.vc, (size_t)n);
+    }
+    c.gs.R = nullptr;
+    PPG_TRY(ar.alloc(s));
+    struct Guard { Arena& a; cudaStream_t s; ~Guard() { a.release(s); } } guard{ar, s};
+    PPG_CUDA(cudaMemsetAsync(c.ows.counter, 0, 4 * sizeof(unsigned), s));
+    PPG_CUDA(cudaMemsetAsync(c.gs.scal, 0, 8 * sizeof(double), s));
+    PPG_CUDA(cudaMemsetAsync(c.gs.Hraw, 0, sizeof(double) * ldh * d, s));
+    std::vector<Step> inner_phi;
+    if (inner) inner_phi = plan_phi(inner->re, inner->im, inner->n_total, false);
+    int nparts = 0;
+    PPG_TRY(launch_norm2_part(v0, n, c.spart, s, &nparts));
+    PPG_TRY(launch_reduce_norm(c.spart, nparts, c.gs.scal, nullptr, s));
+    PPG_TRY(launch_scale(v0, c.V, n, c.gs.scal + 4, s));
+    for (int j = 0; j < d; ++j) {
+        double* vj = c.V + (size_t)j * c.ldv;
+        double* w = c.V + (size_t)(j + 1) * c.ldv;
+        if (inner) {
+            Buffers b{};
+            b.ptr[B_IN] = vj;
+            b.ptr[B_OUT] = w;
+            b.ptr[B_A] = c.va;
+            b.ptr[B_B] = c.vb;
+            b.ptr[B_C] = c.vc;
+            PPG_TRY(run_plan<double>(inner_phi, A->rowptr, A->colind, (const double*)A->vals, n,
+                                     A->nnz, b, s, nullptr));
+        } else {
+            StepArgs<double> a{};
+            a.rowptr = A->rowptr;
+            a.colind = A->colind;
+            a.vals = (const double*)A->vals;
+            a.n = n;
+            a.flags = keep_a_flag(a.n, A->nnz, 8, 3);
+            a.x = vj;
+            a.o0 = w;
+            int32_t g = launch_step<double>(OP_SPMV, a, s);
+            if (g < 0) return g;
+        }
+        PPG_TRY(cgs2_column(c, j, w, true, nullptr));
+        PPG_TRY(launch_finish_column(c.gs, ldh, j, c.ows.h1, c.ows.h2, c.ows.nrm, false, 1.0,
+                                     1e-13, s));
+        PPG_TRY(launch_scale(w, w, n, c.gs.scal + 2, s));
+    }
+    std::vector<double> H((size_t)ldh * d), sc(8);
+    PPG_CUDA(cudaMemcpyAsync(H.data(), c.gs.Hraw, sizeof(double) * ldh * d,
+                             cudaMemcpyDeviceToHost, s));
+    PPG_CUDA(cudaMemcpyAsync(sc.data(), c.gs.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    PPG_CUDA(cudaStreamSynchronize(s));
+    if (Hbar_host) std::memcpy(Hbar_host, H.data(), sizeof(double) * ldh * d);
+    if (!std::isfinite(sc[3]) || sc[3] == 0.0) return PPG_ERR_ARG;   // v0 zero or non-finite
+    const bool brk = sc[5] != 0.0;
+    const int d_eff = brk ? (int)sc[6] + 1 : d;
+    int32_t rc = ppg_roots_from_hessenberg(H.data(), ldh, d_eff, &o, out);
+    if (rc != PPG_OK) return rc;
+    return brk ? PPG_LUCKY_BREAKDOWN : PPG_OK;
+}
+
 static int32_t run_solve(SolveCore& c) {
     const int32_t n = c.A64->n;
     const int64_t nnz = c.A64->nnz;
@@ -541,6 +626,247 @@ static int32_t run_solve(SolveCore& c) {
     return converged ? PPG_OK : PPG_NOT_CONVERGED;
 }
 
+// Restarted GMRES(m) on a polynomial of an operator M, for the two
+// variants of Sections 5.2 and 6:
+//  * double polynomial (inner != NULL): M = phi_1(A) with phi_1 from the
+//    inner roots; the solve runs GMRES on phi_2(M) z = b with phi_2 from
+//    c.roots, accumulates x' = p_2(M) z over the restarts (each restart from
+//    the true residual b - M x'), and returns x = p_1(A) x';
+//  * changing polynomial (rebuild_d > 0): M = A, and the polynomial is
+//    rebuilt by GMRES(rebuild_d) from the current residual at the start of
+//    every cycle.
+// Operator products of a composite M run its Algorithm 1 chain into a work
+// vector, and the outer root step is then applied elementwise.
+static int32_t run_solve_ext(SolveCore& c, const ppg_roots* inner, int rebuild_d) {
+    const int32_t n = c.A64->n;
+    const int64_t nnz = c.A64->nnz;
+    const int m = c.m;
+    const int ldh = m + 1;
+    cudaStream_t s = c.s;
+    const ppg_csr* A = c.A64;
+    const double* vals = (const double*)A->vals;
+    const int64_t launches0 = g_launches;
+    PPG_TRY(setup_device_pool());
+    const int dM = inner ? inner->n_total : 1;
+    std::vector<Step> inner_phi;
+    if (inner) inner_phi = plan_phi(inner->re, inner->im, inner->n_total, false);
+
+    Arena ar;
+    c.ldv = pad_ld(n);
+    double *ia = nullptr, *ib = nullptr, *ic = nullptr, *S = nullptr, *xp = nullptr;
+    ar.add(&c.V, (size_t)c.ldv * (m + 1));
+    ar.add(&c.va, (size_t)n);
+    ar.add(&c.vb, (size_t)n);
+    ar.add(&c.vc, (size_t)n);
+    ar.add(&c.u, (size_t)n);
+    ar.add(&ia, (size_t)n);
+    ar.add(&ib, (size_t)n);
+    ar.add(&ic, (size_t)n);
+    ar.add(&S, (size_t)n);
+    ar.add(&xp, (size_t)n);
+    const int sgrid = spmv_grid_blocks(n);
+    ar.add(&c.spart, (size_t)sgrid + 1024);
+    c.ows.grid = ortho_grid(n);
+    ar.add(&c.ows.part, ortho_part_doubles(c.ows.grid));
+    ar.add(&c.ows.counter, 4);
+    ar.add(&c.ows.h1, ORTHO_MAXC + 2);
+    ar.add(&c.ows.h2, ORTHO_MAXC + 2);
+    ar.add(&c.ows.nrm, 4);
+    ar.add(&c.gs.R, (size_t)ldh * m);
+    ar.add(&c.gs.cs, (size_t)m);
+    ar.add(&c.gs.sn, (size_t)m);
+    ar.add(&c.gs.g, (size_t)m + 1);
+    ar.add(&c.gs.y, (size_t)m);
+    ar.add(&c.gs.scal, 8);
+    c.gs.Hraw = nullptr;
+    PPG_TRY(ar.alloc(s));
+    struct Guard { Arena& a; cudaStream_t s; ~Guard() { a.release(s); } } guard{ar, s};
+    PPG_CUDA(cudaMemsetAsync(c.ows.counter, 0, 4 * sizeof(unsigned), s));
+    PPG_CUDA(cudaMemsetAsync(c.gs.scal, 0, 8 * sizeof(double), s));
+
+    // y = M x
+    auto apply_M = [&](const double* xin, double* yout) -> int32_t {
+        if (inner) {
+            Buffers b{};
+            b.ptr[B_IN] = const_cast<double*>(xin);
+            b.ptr[B_OUT] = yout;
+            b.ptr[B_A] = ia;
+            b.ptr[B_B] = ib;
+            b.ptr[B_C] = ic;
+            return run_plan<double>(inner_phi, A->rowptr, A->colind, vals, n, nnz, b, s, nullptr);
+        }
+        StepArgs<double> a{};
+        a.rowptr = A->rowptr;
+        a.colind = A->colind;
+        a.vals = vals;
+        a.n = n;
+        a.flags = keep_a_flag(n, nnz, 8, 3);
+        a.x = xin;
+        a.o0 = yout;
+        const int32_t g = launch_step<double>(OP_SPMV, a, s);
+        return g < 0 ? g : PPG_OK;
+    };
+    // one polynomial of M (a plan built for a single SpMV per product)
+    auto run_outer = [&](const std::vector<Step>& plan, const Buffers& bufs) -> int32_t {
+        if (!inner)
+            return run_plan<double>(plan, A->rowptr, A->colind, vals, n, nnz, bufs, s, nullptr);
+        for (const Step& st : plan) {
+            double* X = (double*)bufs.ptr[st.x];
+            if (st.op == -1) {   // degree one: P = c1 v (+ P), no product
+                const bool pz = st.flags & F_PZERO;
+                PPG_TRY(launch_axpby<double>(st.c1, X, pz ? 0.0 : 1.0,
+                                             pz ? nullptr : (double*)bufs.ptr[B_P],
+                                             (double*)bufs.ptr[B_P], n, s));
+                continue;
+            }
+            if (st.op == OP_SPMV) {
+                PPG_TRY(apply_M(X, (double*)bufs.ptr[st.o0]));
+                continue;
+            }
+            PPG_TRY(apply_M(X, S));
+            StepArgs<double> a{};
+            a.n = n;
+            a.a0 = st.a0 >= 0 ? (const double*)bufs.ptr[st.a0] : nullptr;
+            a.a1 = st.a1 >= 0 ? (const double*)bufs.ptr[st.a1] : nullptr;
+            a.a2 = st.a2 >= 0 ? (const double*)bufs.ptr[st.a2] : nullptr;
+            a.o0 = st.o0 >= 0 ? (double*)bufs.ptr[st.o0] : nullptr;
+            a.o1 = st.o1 >= 0 ? (double*)bufs.ptr[st.o1] : nullptr;
+            a.c1 = st.c1;
+            a.c2 = st.c2;
+            a.c3 = st.c3;
+            a.flags = st.flags;
+            const int32_t g = launch_ew_step<double>(st.op, a, S, s);
+            if (g < 0) return g;
+        }
+        return PPG_OK;
+    };
+
+    c.st = ppg_stats{};
+    double* scal_h = nullptr;
+    PPG_TRY(status_buffer(&scal_h));
+    int nparts = 0;
+    PPG_TRY(launch_norm2_part(c.b, n, c.spart, s, &nparts));
+    PPG_TRY(launch_reduce_norm(c.spart, nparts, c.gs.scal, c.gs.g, s));
+    PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PPG_CUDA(cudaStreamSynchronize(s));
+    const double bnorm = scal_h[3];
+    c.st.dots += 1;
+    if (!std::isfinite(bnorm)) return PPG_ERR_NONFINITE;
+    double* xs = inner ? xp : c.x;   // the iterate of the outer solve
+    PPG_TRY(launch_fill(xs, 0.0, n, s));
+    if (bnorm == 0.0) {
+        PPG_TRY(launch_fill(c.x, 0.0, n, s));
+        PPG_CUDA(cudaStreamSynchronize(s));
+        c.st.converged = 1;
+        c.st.true_relres = 0.0;
+        c.st.launches = g_launches - launches0;
+        return PPG_OK;
+    }
+    PPG_CUDA(cudaMemcpyAsync(c.V, c.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double beta = bnorm;
+    c.st.true_relres = 1.0;
+    bool converged = false;
+
+    // the outer polynomial (rebuilt every cycle in the changing form)
+    std::vector<double> rre, rim;
+    ppg_roots rr{};
+    const ppg_roots* outer = c.roots;
+    Buffers pb{}, phib{};
+    phib.ptr[B_A] = c.va;
+    phib.ptr[B_B] = c.vb;
+    phib.ptr[B_C] = c.vc;
+    std::vector<Step> phi_plan, p_plan;
+    if (!rebuild_d) {
+        phi_plan = plan_phi(outer->re, outer->im, outer->n_total, false);
+        p_plan = plan_p(outer->re, outer->im, outer->n_total, true);
+    }
+    const int max_cycles = c.opts.max_cycles > 0 ? c.opts.max_cycles : 10000;
+    for (int cyc = 0; cyc < max_cycles && !converged; ++cyc) {
+        c.st.cycles += 1;
+        if (rebuild_d) {
+            // Section 5.2: GMRES(rebuild_d) from the current residual r (in V_0)
+            const int cap = 4 * rebuild_d + 8;
+            rre.assign(cap, 0.0);
+            rim.assign(cap, 0.0);
+            rr = ppg_roots{0, 0, 0, cap, rre.data(), rim.data(), nullptr};
+            const int32_t rc = build_core(A, rebuild_d, c.V, c.opts, nullptr, &rr, nullptr, s);
+            if (rc < 0) return rc;
+            outer = &rr;
+            phi_plan = plan_phi(rr.re, rr.im, rr.n_total, false);
+            p_plan = plan_p(rr.re, rr.im, rr.n_total, true);
+            c.st.mvps += rebuild_d;
+        }
+        const int d = outer->n_total;
+        PPG_TRY(launch_scale(c.V, c.V, n, c.gs.scal + 4, s));
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = c.V + (size_t)j * c.ldv;
+            double* w = c.V + (size_t)(j + 1) * c.ldv;
+            phib.ptr[B_IN] = vj;
+            phib.ptr[B_OUT] = w;
+            PPG_TRY(run_outer(phi_plan, phib));
+            c.st.mvps += (int64_t)d * dM;
+            PPG_TRY(cgs2_column(c, j, w, false, nullptr));
+            PPG_TRY(launch_finish_column(c.gs, ldh, j, c.ows.h1, c.ows.h2, c.ows.nrm, true,
+                                         bnorm, 0.0, s));
+            PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 4 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+            PPG_CUDA(cudaStreamSynchronize(s));
+            c.st.iters += 1;
+            c.st.dots += 2 * (j + 1) + 1;
+            k = j + 1;
+            const double est = scal_h[0], hn = scal_h[1];
+            c.st.est_relres = est;
+            if (!std::isfinite(est) || !std::isfinite(hn)) return PPG_ERR_NONFINITE;
+            if (est <= c.tol || hn == 0.0) break;
+            if (j + 1 < m) PPG_TRY(launch_scale(w, w, n, c.gs.scal + 2, s));
+        }
+        PPG_TRY(launch_backsolve(c.gs, ldh, k, s));
+        PPG_TRY(launch_gemv_acc<double>(c.V, c.ldv, k, c.gs.y, c.u, n, false, s));
+        pb.ptr[B_IN] = c.u;
+        pb.ptr[B_P] = xs;
+        pb.ptr[B_A] = c.va;
+        pb.ptr[B_B] = c.vb;
+        pb.ptr[B_C] = c.vc;
+        PPG_TRY(run_outer(p_plan, pb));
+        c.st.mvps += (int64_t)(d - 1) * dM;
+        // true residual r = b - M x' into V_0
+        PPG_TRY(apply_M(xs, S));
+        StepArgs<double> a{};
+        a.n = n;
+        a.a0 = c.b;
+        a.o0 = c.V;
+        a.part = c.spart;
+        const int32_t g = launch_ew_step<double>(OP_RESID, a, S, s);
+        if (g < 0) return g;
+        PPG_TRY(launch_reduce_norm(c.spart, g, c.gs.scal, c.gs.g, s));
+        c.st.mvps += dM;
+        c.st.dots += 1;
+        PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PPG_CUDA(cudaStreamSynchronize(s));
+        beta = scal_h[3];
+        if (!std::isfinite(beta)) return PPG_ERR_NONFINITE;
+        c.st.true_relres = beta / bnorm;
+        converged = c.st.true_relres <= c.tol;
+    }
+    if (inner) {
+        // x = p_1(A) x'
+        Buffers b{};
+        b.ptr[B_IN] = xp;
+        b.ptr[B_P] = c.x;
+        b.ptr[B_A] = ia;
+        b.ptr[B_B] = ib;
+        b.ptr[B_C] = ic;
+        PPG_TRY(run_plan<double>(plan_p(inner->re, inner->im, inner->n_total, false), A->rowptr,
+                                 A->colind, vals, n, nnz, b, s, nullptr));
+        c.st.mvps += dM - 1;
+        PPG_CUDA(cudaStreamSynchronize(s));
+    }
+    c.st.converged = converged ? 1 : 0;
+    c.st.launches = g_launches - launches0;
+    return converged ? PPG_OK : PPG_NOT_CONVERGED;
+}
+
 }  // namespace ppg
 
 using namespace ppg;
@@ -703,66 +1029,19 @@ int32_t ppg_build_poly(const ppg_csr* A, int32_t d, const double* v0, const ppg_
     ppg_opts o;
     ppg_default_opts(&o);
     if (opts) o = *opts;
-    PPG_TRY(setup_device_pool());
-    cudaStream_t s = (cudaStream_t)stream;
-    const int32_t n = A->n;
-    const int ldh = d + 1;
-    SolveCore c{};
-    c.A64 = A;
-    c.s = s;
-    c.ldv = pad_ld(n);
-    Arena ar;
-    ar.add(&c.V, (size_t)c.ldv * (d + 1));
-    const int sg = spmv_grid_blocks(n);
-    ar.add(&c.spart, (size_t)sg + 1024);
-    c.ows.grid = ortho_grid(n);
-    ar.add(&c.ows.part, ortho_part_doubles(c.ows.grid));
-    ar.add(&c.ows.counter, 4);
-    ar.add(&c.ows.h1, ORTHO_MAXC + 2);
-    ar.add(&c.ows.h2, ORTHO_MAXC + 2);
-    ar.add(&c.ows.nrm, 4);
-    ar.add(&c.gs.Hraw, (size_t)ldh * d);
-    ar.add(&c.gs.scal, 8);
-    c.gs.R = nullptr;
-    PPG_TRY(ar.alloc(s));
-    struct Guard { Arena& a; cudaStream_t s; ~Guard() { a.release(s); } } guard{ar, s};
-    PPG_CUDA(cudaMemsetAsync(c.ows.counter, 0, 4 * sizeof(unsigned), s));
-    PPG_CUDA(cudaMemsetAsync(c.gs.scal, 0, 8 * sizeof(double), s));
-    PPG_CUDA(cudaMemsetAsync(c.gs.Hraw, 0, sizeof(double) * ldh * d, s));
-    int nparts = 0;
-    PPG_TRY(launch_norm2_part(v0, n, c.spart, s, &nparts));
-    PPG_TRY(launch_reduce_norm(c.spart, nparts, c.gs.scal, nullptr, s));
-    PPG_TRY(launch_scale(v0, c.V, n, c.gs.scal + 4, s));
-    for (int j = 0; j < d; ++j) {
-        double* vj = c.V + (size_t)j * c.ldv;
-        double* w = c.V + (size_t)(j + 1) * c.ldv;
-        StepArgs<double> a{};
-        a.rowptr = A->rowptr;
-        a.colind = A->colind;
-        a.vals = (const double*)A->vals;
-        a.n = n;
-        a.flags = keep_a_flag(a.n, A->nnz, 8, 3);
-        a.x = vj;
-        a.o0 = w;
-        int32_t g = launch_step<double>(OP_SPMV, a, s);
-        if (g < 0) return g;
-        PPG_TRY(cgs2_column(c, j, w, true, nullptr));
-        PPG_TRY(launch_finish_column(c.gs, ldh, j, c.ows.h1, c.ows.h2, c.ows.nrm, false, 1.0,
-                                     1e-13, s));
-        PPG_TRY(launch_scale(w, w, n, c.gs.scal + 2, s));
-    }
-    std::vector<double> H((size_t)ldh * d), sc(8);
-    PPG_CUDA(cudaMemcpyAsync(H.data(), c.gs.Hraw, sizeof(double) * ldh * d,
-                             cudaMemcpyDeviceToHost, s));
-    PPG_CUDA(cudaMemcpyAsync(sc.data(), c.gs.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
-    PPG_CUDA(cudaStreamSynchronize(s));
-    if (Hbar_host) std::memcpy(Hbar_host, H.data(), sizeof(double) * ldh * d);
-    if (!std::isfinite(sc[3]) || sc[3] == 0.0) return PPG_ERR_ARG;   // v0 zero or non-finite
-    const bool brk = sc[5] != 0.0;
-    const int d_eff = brk ? (int)sc[6] + 1 : d;
-    int32_t rc = ppg_roots_from_hessenberg(H.data(), ldh, d_eff, &o, out);
-    if (rc != PPG_OK) return rc;
-    return brk ? PPG_LUCKY_BREAKDOWN : PPG_OK;
+    return build_core(A, d, v0, o, nullptr, out, Hbar_host, (cudaStream_t)stream);
+}
+
+int32_t ppg_build_poly_composite(const ppg_csr* A, const ppg_roots* inner, int32_t d,
+                                 const double* v0, const ppg_opts* opts, ppg_roots* out,
+                                 double* Hbar_host, void* stream) {
+    PPG_TRY(check_csr(A, PPG_F64));
+    if (!v0 || !out || d < 1 || d + 1 > ORTHO_MAXC) return PPG_ERR_ARG;
+    if (inner) PPG_TRY(check_roots(inner));
+    ppg_opts o;
+    ppg_default_opts(&o);
+    if (opts) o = *opts;
+    return build_core(A, d, v0, o, inner, out, Hbar_host, (cudaStream_t)stream);
 }
 
 int32_t ppg_solve(const ppg_csr* A, const ppg_roots* r, const double* b, double* x, int32_t m,
@@ -808,6 +1087,51 @@ int32_t ppg_solve_flex(const ppg_csr* A64, const ppg_csr* A32, const ppg_roots* 
     c.flex = true;
     c.s = (cudaStream_t)stream;
     int32_t rc = run_solve(c);
+    if (stats) *stats = c.st;
+    return rc;
+}
+
+int32_t ppg_solve_double(const ppg_csr* A, const ppg_roots* r1, const ppg_roots* r2,
+                         const double* b, double* x, int32_t m, double tol, const ppg_opts* opts,
+                         ppg_stats* stats, void* stream) {
+    PPG_TRY(check_csr(A, PPG_F64));
+    PPG_TRY(check_roots(r1));
+    PPG_TRY(check_roots(r2));
+    if (!b || !x || b == x || m < 1 || m + 1 > ORTHO_MAXC || !(tol > 0.0)) return PPG_ERR_ARG;
+    SolveCore c{};
+    c.A64 = A;
+    c.roots = r2;
+    c.b = b;
+    c.x = x;
+    c.m = m;
+    c.tol = tol;
+    ppg_default_opts(&c.opts);
+    if (opts) c.opts = *opts;
+    if (c.opts.x0_given) return PPG_ERR_ARG;
+    c.s = (cudaStream_t)stream;
+    const int32_t rc = run_solve_ext(c, r1, 0);
+    if (stats) *stats = c.st;
+    return rc;
+}
+
+int32_t ppg_solve_chpoly(const ppg_csr* A, int32_t d, const double* b, double* x, int32_t m,
+                         double tol, const ppg_opts* opts, ppg_stats* stats, void* stream) {
+    PPG_TRY(check_csr(A, PPG_F64));
+    if (!b || !x || b == x || d < 1 || d + 1 > ORTHO_MAXC || m < 1 || m + 1 > ORTHO_MAXC ||
+        !(tol > 0.0))
+        return PPG_ERR_ARG;
+    SolveCore c{};
+    c.A64 = A;
+    c.roots = nullptr;
+    c.b = b;
+    c.x = x;
+    c.m = m;
+    c.tol = tol;
+    ppg_default_opts(&c.opts);
+    if (opts) c.opts = *opts;
+    if (c.opts.x0_given) return PPG_ERR_ARG;
+    c.s = (cudaStream_t)stream;
+    const int32_t rc = run_solve_ext(c, nullptr, d);
     if (stats) *stats = c.st;
     return rc;
 }

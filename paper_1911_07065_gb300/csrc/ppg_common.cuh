@@ -140,6 +140,11 @@ struct StepArgs {
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s);
 
+// a root step with the operator product precomputed in prodv (composite
+// operators); returns the grid (= partial sums for OP_RESID) or a status
+template <typename T>
+int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_t s);
+
 // F_KEEP_A when the matrix plus `nvec` work vectors fit comfortably in L2
 int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec);
 

@@ -52,6 +52,48 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// The epilogue of one row: the root update of the step, given s = (A x)[r]
+// and the row's inputs e0 = a0[r], e1 = a1[r], e2 = a2[r].
+template <typename T, int OP>
+__device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T s, T e0, T e1,
+                                              T e2, double& sq) {
+    if constexpr (OP == OP_SPMV) {
+        a.o0[r] = s;
+    } else if constexpr (OP == OP_RESID) {
+        const T v = e0 - s;
+        a.o0[r] = v;
+        sq += (double)v * (double)v;
+    } else if constexpr (OP == OP_PHI_REAL) {
+        const T pin = fma(-a.c1, s, e0);
+        a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
+    } else if constexpr (OP == OP_PHI_PAIR2) {
+        // pi' = pi + c2 (A prod - 2a prod)
+        const T t = fma(-a.c1, e0, s);
+        const T pin = fma(a.c2, t, e1);
+        a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
+    } else if constexpr (OP == OP_P_REAL) {
+        const T pnew = (a.flags & F_PZERO) ? a.c1 * e0 : fma(a.c1, e0, e1);
+        const T prodn = fma(-a.c1, s, e0);
+        if (a.flags & F_FINAL) {
+            a.o0[r] = fma(a.c3, prodn, pnew);
+        } else {
+            a.o0[r] = pnew;
+            a.o1[r] = prodn;
+        }
+    } else if constexpr (OP == OP_P_PAIR1) {
+        const T tmp = fma(a.c1, e0, -s);
+        a.o0[r] = (a.flags & F_PZERO) ? a.c2 * tmp : fma(a.c2, tmp, e1);
+        if (!(a.flags & F_NO_O1)) a.o1[r] = tmp;
+    } else if constexpr (OP == OP_P_PAIR2) {
+        const T prodn = fma(-a.c2, s, e0);
+        if (a.flags & F_FINAL) {
+            a.o0[r] = fma(a.c3, prodn, e1);
+        } else {
+            a.o0[r] = prodn;
+        }
+    }
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(SPMV_ROWS)
 k_spmv_step(const StepArgs<T> a) {
@@ -126,45 +168,7 @@ k_spmv_step(const StepArgs<T> a) {
     }
 
     double sq = 0.0;
-    if (live) {
-        const int64_t r = rr;
-        const T s = acc;
-        if constexpr (OP == OP_SPMV) {
-            a.o0[r] = s;
-        } else if constexpr (OP == OP_RESID) {
-            const T v = e0 - s;
-            a.o0[r] = v;
-            sq = (double)v * (double)v;
-        } else if constexpr (OP == OP_PHI_REAL) {
-            const T pin = fma(-a.c1, s, e0);
-            a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
-        } else if constexpr (OP == OP_PHI_PAIR2) {
-            // pi' = pi + c2 (A prod - 2a prod)
-            const T t = fma(-a.c1, e0, s);
-            const T pin = fma(a.c2, t, e1);
-            a.o0[r] = (a.flags & F_FINAL) ? e2 - pin : pin;
-        } else if constexpr (OP == OP_P_REAL) {
-            const T pnew = (a.flags & F_PZERO) ? a.c1 * e0 : fma(a.c1, e0, e1);
-            const T prodn = fma(-a.c1, s, e0);
-            if (a.flags & F_FINAL) {
-                a.o0[r] = fma(a.c3, prodn, pnew);
-            } else {
-                a.o0[r] = pnew;
-                a.o1[r] = prodn;
-            }
-        } else if constexpr (OP == OP_P_PAIR1) {
-            const T tmp = fma(a.c1, e0, -s);
-            a.o0[r] = (a.flags & F_PZERO) ? a.c2 * tmp : fma(a.c2, tmp, e1);
-            if (!(a.flags & F_NO_O1)) a.o1[r] = tmp;
-        } else if constexpr (OP == OP_P_PAIR2) {
-            const T prodn = fma(-a.c2, s, e0);
-            if (a.flags & F_FINAL) {
-                a.o0[r] = fma(a.c3, prodn, e1);
-            } else {
-                a.o0[r] = prodn;
-            }
-        }
-    }
+    if (live) step_epilogue<T, OP>(a, rr, acc, e0, e1, e2, sq);
     if constexpr (OP == OP_RESID) {
         // deterministic block reduction of ||r||^2
         for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
@@ -177,6 +181,56 @@ k_spmv_step(const StepArgs<T> a) {
         }
     }
 }
+
+// A root step whose operator product s = (M x)[r] was computed beforehand
+// (M a composite operator such as phi_1(A)): the same epilogue as the
+// fused kernel, one thread per row.
+template <typename T, int OP>
+__global__ void __launch_bounds__(SPMV_ROWS)
+k_ew_step(const StepArgs<T> a, const T* __restrict__ prodv) {
+    __shared__ double sred[SPMV_ROWS / 32];
+    const int tid = threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * SPMV_ROWS + tid;
+    const bool live = r < a.n;
+    double sq = 0.0;
+    if (live) {
+        const T e0 = a.a0 ? __ldg(a.a0 + r) : T(0);
+        const T e1 = (a.a1 && !(a.flags & F_PZERO)) ? a.a1[r] : T(0);
+        const T e2 = (a.a2 && (a.flags & F_FINAL)) ? __ldg(a.a2 + r) : T(0);
+        step_epilogue<T, OP>(a, r, __ldg(prodv + r), e0, e1, e2, sq);
+    }
+    if constexpr (OP == OP_RESID) {
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+        if ((tid & 31) == 0) sred[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < SPMV_ROWS / 32; ++w) t += sred[w];
+            a.part[blockIdx.x] = t;
+        }
+    }
+}
+
+template <typename T>
+int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_t s) {
+    if (a.n <= 0) return 0;
+    const int grid = (a.n + SPMV_ROWS - 1) / SPMV_ROWS;
+    switch (op) {
+        case OP_RESID: k_ew_step<T, OP_RESID><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        case OP_PHI_REAL: k_ew_step<T, OP_PHI_REAL><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        case OP_PHI_PAIR2: k_ew_step<T, OP_PHI_PAIR2><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        case OP_P_REAL: k_ew_step<T, OP_P_REAL><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        case OP_P_PAIR1: k_ew_step<T, OP_P_PAIR1><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        case OP_P_PAIR2: k_ew_step<T, OP_P_PAIR2><<<grid, SPMV_ROWS, 0, s>>>(a, prodv); break;
+        default: return PPG_ERR_ARG;
+    }
+    ++g_launches;
+    int32_t rc = check_launch("k_ew_step");
+    return rc < 0 ? rc : grid;
+}
+
+template int32_t launch_ew_step<double>(int, const StepArgs<double>&, const double*,
+                                        cudaStream_t);
 
 int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
 
