@@ -274,8 +274,13 @@ def run_ours(args, rank, local, world):
     stream = torch.cuda.current_stream()
 
     def step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         R = ppg.build_poly(A, P.d, v0)
+        e1.record(stream)
         _, st = ppg.solve(A, b, P.m, P.tol, roots=R, timing=True, out=x)
+        st["build_ms"] = e0.elapsed_time(e1)
         return R, st
 
     for _ in range(args.warmup):
@@ -352,7 +357,8 @@ def run_ours(args, rank, local, world):
                    "l2": "flushed (512 MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "iters": st["iters"], "cycles": st["cycles"], "mvps": st["mvps"], "dots": st["dots"],
-        "solve_breakdown_ms": {"spmv_root_chains": round(st["poly_ms"], 3),
+        "solve_breakdown_ms": {"build_poly": round(st["build_ms"], 3),
+                               "spmv_root_chains": round(st["poly_ms"], 3),
                                "cgs2_givens": round(st["ortho_ms"], 3)},
         "true_relres": rel, "converged": bool(st["converged"]),
         "roofline": {"bound": "hbm", "kernel": "k_spmv_step (fused SpMV-root, Alg 1/3)",
