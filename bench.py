@@ -25,7 +25,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -506,6 +505,7 @@ def run_profile_case(name):
     (n = 4e6, FP64; the matrix and vectors exceed L2), six real roots;
     ``arnoldi_cd2d_2000``: the degree-30 polynomial construction on it (CGS2);
     ``phi_cd2d_1000``: two applications of the benchmark's own polynomial;
+    ``batched_64x4``: one call of the batching form on its full workload;
     ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix."""
     import numpy as np
     import torch
@@ -529,6 +529,18 @@ def run_profile_case(name):
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
         y = ppg.apply_phi(Ad, R, v)
         y = ppg.apply_phi(Ad, R, y)
+    elif name == "batched_64x4":
+        # the batching workload: 64 systems x 4 right-hand sides, one call
+        probs = synth.batch_problem(nsys=64, seed=104)
+        dA = [ppg.CSR.from_host(A.rowptr, A.colind, A.vals) for A, _, _ in probs]
+        dB = [torch.from_numpy(np.ascontiguousarray(B)).cuda() for _, B, _ in probs]
+        dv = [torch.from_numpy(v).cuda() for _, _, v in probs]
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            Xs, _ = ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10)
+        torch.cuda.synchronize()
+        A = probs[0][0]
+        y = Xs[0]
     elif name == "arnoldi_cd2d_2000":
         # the polynomial's Arnoldi (d = 30) on n = 4e6: CGS2 passes over up to
         # 31 basis columns of 32 MB

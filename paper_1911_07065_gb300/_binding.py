@@ -9,8 +9,8 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from dataclasses import dataclass
-from typing import Optional
+
+
 
 import numpy as np
 

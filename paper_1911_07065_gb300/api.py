@@ -11,7 +11,7 @@ from typing import Optional, Tuple
 import numpy as np
 import torch
 
-from ._binding import (PPG_F32, PPG_F64, PPGError, Roots, check, default_opts, lib, ppg_roots,
+from ._binding import (PPG_F32, PPG_F64, Roots, check, default_opts, lib, ppg_roots,
                        ppg_csr, ppg_stats, csr_validate_host, _dp)
 
 
