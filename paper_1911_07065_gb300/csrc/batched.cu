@@ -127,18 +127,35 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
     for (int i = 0; i < NR; ++i) acc[i] = T(0);
     for (int32_t c0 = k0; c0 < k1; c0 += BCHUNK) {
         const int32_t c1 = min(k1, c0 + BCHUNK);
+        // asynchronous, coalesced staging of the tile's values and columns
         for (int32_t k = c0 + tid; k < c1; k += rows) {
-            sval[k - c0] = __ldcs(vals + k);
-            scol[k - c0] = __ldcs(colind + k);
+            const unsigned sv_ = (unsigned)__cvta_generic_to_shared(sval + (k - c0));
+            const unsigned sc_ = (unsigned)__cvta_generic_to_shared(scol + (k - c0));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sv_), "l"(vals + k),
+                         "n"(sizeof(T)) : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sc_), "l"(colind + k)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        const int32_t lo = max(lo_r, c0), hi = min(hi_r, c1);
-        for (int32_t k = lo; k < hi; ++k) {
-            T xv[NR];
-            ld_rhs<T, NR>(x + (int64_t)scol[k - c0] * NR, xv);
-            const T v = sval[k - c0];
+        const int32_t lo = max(lo_r, c0) - c0, hi = min(hi_r, c1) - c0;
+        int32_t k = lo;
+        // one FMA per nonzero and right-hand side, the gathers of two
+        // nonzeros (2 NR values) in flight before their multiply-adds
+        for (; k + 2 <= hi; k += 2) {
+            T x0[NR], x1[NR];
+            ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
+            ld_rhs<T, NR>(x + (int64_t)scol[k + 1] * NR, x1);
+            const T v0 = sval[k], v1 = sval[k + 1];
 #pragma unroll
-            for (int i = 0; i < NR; ++i) acc[i] = fma(v, xv[i], acc[i]);
+            for (int i = 0; i < NR; ++i) acc[i] = fma(v1, x1[i], fma(v0, x0[i], acc[i]));
+        }
+        if (k < hi) {
+            T x0[NR];
+            ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
+            const T v0 = sval[k];
+#pragma unroll
+            for (int i = 0; i < NR; ++i) acc[i] = fma(v0, x0[i], acc[i]);
         }
         __syncthreads();
     }
