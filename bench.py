@@ -408,6 +408,51 @@ def _timed(torch, fn):
     return out, e0.elapsed_time(e1)
 
 
+def spmv_yardstick(device, A64, A32, n):
+    """One plain SpMV y = A x on the 160^3 matrix (FP64 and FP32): this
+    library's root-step kernel against cuSPARSE (through torch.sparse_csr),
+    both with L2 flushed before every timed call; GB/s of the CSR bytes
+    plus x read and y written.  A yardstick only: cuSPARSE is not on the
+    solver's path."""
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=device)
+    out = {}
+    for A, tag in ((A64, "f64"), (A32, "f32")):
+        es = A.vals.element_size()
+        by = A.nnz * (es + 4) + 4 * (n + 1) + 2 * n * es
+        x = torch.randn(n, dtype=A.vals.dtype, device=device)
+        y = torch.empty_like(x)
+        S = torch.sparse_csr_tensor(A.rowptr, A.colind, A.vals, (n, n))
+
+        def t_of(fn, reps=10):
+            ts = []
+            for _ in range(reps + 3):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ts = sorted(ts[3:])
+            return ts[len(ts) // 2]
+        t_ours = t_of(lambda: ppg.spmv(A, x, out=y))
+        ref = y.clone()
+        t_cusp = t_of(lambda: torch.mv(S, x))
+        ycs = torch.mv(S, x)
+        rel = float(torch.linalg.norm(ycs - ref) / torch.linalg.norm(ref))
+        out[tag] = {"bytes": by, "ours_ms": round(t_ours, 4), "cusparse_ms": round(t_cusp, 4),
+                    "ours_gbs": round(by / (t_ours * 1e-3) / 1e9, 1),
+                    "cusparse_gbs": round(by / (t_cusp * 1e-3) / 1e9, 1),
+                    "rel_diff": rel}
+    del flush
+    return out
+
+
 def measure_forms(device):
     """The three forms beside the plain FP64 method, each against the plain
     FP64 PP-GMRES on the same GPU at relative residual 1e-10 (one run each,
@@ -430,9 +475,22 @@ def measure_forms(device):
     (x32, s32), t32 = _timed(torch, lambda: ppg.solve_flex(A64, A32, b, R, P.m, P.tol))
     ppg.solve(A64, b, P.m, P.tol, roots=R)
     (x64, s64), t64 = _timed(torch, lambda: ppg.solve(A64, b, P.m, P.tol, roots=R))
+    # root-step chains alone (library CUDA events around each chain): the
+    # 160^3 working set (matrix 245 MB in FP32, 355 MB in FP64) exceeds L2
+    _, f32t = ppg.solve_flex(A64, A32, b, R, P.m, P.tol, timing=True)
+    _, f64t = ppg.solve(A64, b, P.m, P.tol, roots=R, timing=True)
+    hbm = _peaks()[0]
+
+    def chain_bw(st, what):
+        gbs = st["poly_bytes"] / (st["poly_ms"] * 1e-3) / 1e9
+        return {"chains": what, "achieved_gbs": round(gbs, 1),
+                "frac": round(gbs / hbm, 4), "peak_gbs": hbm,
+                "launches": st["poly_launches"], "ms": round(st["poly_ms"], 2)}
     As = P.A.to_scipy()
     xh32, xh64 = x32.cpu().numpy(), x64.cpu().numpy()
     out["precision_cd3d_160"] = {
+        "p_fp32_roofline": chain_bw(f32t, "p(A) v_j in FP32 (Algorithm 3), every outer step"),
+        "phi_fp64_roofline": chain_bw(f64t, "phi(A) v_j in FP64 (Algorithm 1) and p(A) u per restart"),
         "n": P.A.n, "degree": R.n_total, "build_ms": round(t_build, 2),
         "fp32_inner_ms": round(t32, 2), "fp32_inner_iters": s32["iters"],
         "fp32_inner_relres": float(np.linalg.norm(P.b - As @ xh32) / np.linalg.norm(P.b)),
@@ -440,6 +498,7 @@ def measure_forms(device):
         "fp64_relres": float(np.linalg.norm(P.b - As @ xh64) / np.linalg.norm(P.b)),
         "rel_diff_fp32_vs_fp64": float(np.linalg.norm(xh32 - xh64) / np.linalg.norm(xh64)),
     }
+    out["spmv_yardstick"] = spmv_yardstick(device, A64, A32, P.A.n)
     del A64, A32, x32, x64
     # batching form: 64 systems x 4 right-hand sides in one call
     probs = synth.batch_problem(nsys=64, seed=104)

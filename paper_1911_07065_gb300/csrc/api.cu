@@ -497,11 +497,12 @@ static int32_t run_solve(SolveCore& c) {
         for (int j = 0; j < m; ++j) {
             double* vj = c.V + (size_t)j * c.ldv;
             double* w = c.V + (size_t)(j + 1) * c.ldv;
+            // the polynomial timer covers the root steps only, not the cast
+            if (c.flex) PPG_TRY(launch_cast_f64_f32(vj, c.v32, n, s));
             ev_poly.start(s);
             if (c.flex) {
                 // z_j = p(A) v_j in FP32, then w = A64 z_j
                 float* zj = c.Z32 + (size_t)j * c.ldv;
-                PPG_TRY(launch_cast_f64_f32(vj, c.v32, n, s));
                 if (pp) {
                     Buffers fb{};
                     fb.ptr[B_IN] = c.v32;

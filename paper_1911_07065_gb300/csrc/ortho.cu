@@ -14,6 +14,8 @@
 // shuffles for all eight, and the last CTA to finish sums the per-CTA
 // partials in a fixed order (deterministic; the counter resets itself, no
 // waiting, no extra launch).
+#include <atomic>
+
 #include "ppg_common.cuh"
 
 namespace ppg {
@@ -114,8 +116,10 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     __shared__ double sred[ORTHO_WARPS][DOT_CH];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nvals = ncol + (with_self ? 1 : 0);
-    const int c0 = blockIdx.y * DOT_CH;
-    const int nq = min(DOT_CH, nvals - c0);
+    // gridDim.y = ceil(nvals / 8) chunks of near-equal width (at most 8), so
+    // no CTA of the single wave is left with a narrow remainder
+    const int c0 = (int)(blockIdx.y * (unsigned)nvals / gridDim.y);
+    const int nq = (int)((blockIdx.y + 1) * (unsigned)nvals / gridDim.y) - c0;
     const double* col[DOT_CH];
 #pragma unroll
     for (int q = 0; q < DOT_CH; ++q) {
@@ -142,7 +146,7 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     warp_reduce8(acc, lane);
     if ((lane & 3) == 0) sred[warp][lane >> 2] = acc[0];
     __syncthreads();
-    if (tid < DOT_CH && c0 + tid < nvals) {
+    if (tid < nq) {
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < ORTHO_WARPS; ++k) t += sred[k][tid];
@@ -175,17 +179,27 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     __syncthreads();
     double nacc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
-    for (int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid; r < n; r += stride) {
+    int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
+    // two rows per trip: two independent FMA chains, 2 loads per column in
+    // flight, exactly one FMA per element of V
+    for (; r + stride < n; r += 2 * stride) {
         double s0 = 0.0, s1 = 0.0;
-        int c = 0;
-        for (; c + 1 < ncol; c += 2) {
-            s0 = fma(__ldcs(V + c * ldv + r), sh[c], s0);
-            s1 = fma(__ldcs(V + (c + 1) * ldv + r), sh[c + 1], s1);
+        for (int c = 0; c < ncol; ++c) {
+            const double hc = sh[c];
+            s0 = fma(__ldcs(V + c * ldv + r), hc, s0);
+            s1 = fma(__ldcs(V + c * ldv + r + stride), hc, s1);
         }
-        if (c < ncol) s0 = fma(__ldcs(V + c * ldv + r), sh[c], s0);
-        const double wn = w[r] - (s0 + s1);
-        w[r] = wn;
-        nacc = fma(wn, wn, nacc);
+        const double w0 = w[r] - s0, w1 = w[r + stride] - s1;
+        w[r] = w0;
+        w[r + stride] = w1;
+        nacc = fma(w1, w1, fma(w0, w0, nacc));
+    }
+    if (r < n) {
+        double s0 = 0.0;
+        for (int c = 0; c < ncol; ++c) s0 = fma(__ldcs(V + c * ldv + r), sh[c], s0);
+        const double w0 = w[r] - s0;
+        w[r] = w0;
+        nacc = fma(w0, w0, nacc);
     }
     if (!with_norm) return;
     nacc = warp_sum(nacc);
@@ -203,11 +217,41 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     }
 }
 
+// CTAs of a kernel resident at once on the current device (occupancy x
+// SMs), cached per device and kernel slot
+template <typename K>
+static int resident_ctas(K kernel, int slot) {
+    static std::atomic<int> cached[16][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
+    int v = cached[dev][slot].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int occ = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, ORTHO_THREADS, 0) !=
+                cudaSuccess || occ < 1)
+            occ = 4;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1)
+            sms = 152;
+        v = occ * sms;
+        cached[dev][slot].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+static int mdot_slots() { return resident_ctas(k_mdot, 0); }
+
 int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, int32_t n,
                        bool with_self, double* h_out, const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol + 1 > ORTHO_MAXC + 2) return PPG_ERR_ARG;
     const int nvals = ncol + (with_self ? 1 : 0);
-    const dim3 grid(ws.grid, (nvals + DOT_CH - 1) / DOT_CH);
+    const int nch = (nvals + DOT_CH - 1) / DOT_CH;
+    // row blocks x column chunks = one full wave of resident CTAs (at least
+    // two rows per thread; the partial-sum buffer holds 1216 row blocks)
+    const int gx = max(1, min(min(mdot_slots() / nch, (n + 2 * ORTHO_THREADS - 1) /
+                                                          (2 * ORTHO_THREADS)),
+                              152 * 8));
+    (void)ws.grid;
+    const dim3 grid(gx, nch);
     const cudaError_t e = launch_pdl(k_mdot, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
                                      with_self ? 1 : 0, ws.part, ws.counter, h_out);
     ++g_launches;
@@ -219,7 +263,11 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
                           const double* hin, bool with_norm, double* nrm_out,
                           const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
-    const int grid = max(1, min((n + ORTHO_THREADS - 1) / ORTHO_THREADS, 152 * 8));
+    // one wave of resident CTAs, at least two rows per thread, at most the
+    // 1216 row blocks the partial-sum buffer holds
+    const int grid = max(1, min(min(resident_ctas(k_gemv_sub, 1),
+                                    (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
+                                152 * 8));
     const cudaError_t e = launch_pdl(k_gemv_sub, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv,
                                      ncol, w, n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1,
                                      nrm_out);

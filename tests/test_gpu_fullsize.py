@@ -3,8 +3,9 @@ benchmark times (run with -m gpu).
 
 * 2-D convection-diffusion 1000 x 1000 (n = 1e6): p(A) v against the oracle
   on seeded vectors with the oracle's own roots, the device-built roots
-  against the oracle's, and the full PP-GMRES solve checked by its true
-  residual computed on the host.
+  against the oracle's, the full PP-GMRES solve checked by its true
+  residual computed on the host, and the residual history of the first two
+  restart cycles against the oracle's.
 * 3-D convection-diffusion 160^3 (n = 4.1e6): FP32 p(A) v against the
   oracle's float32 Algorithm 3 (as accurate as it, both against FP64), and the FP32-inner flexible solve checked by
   its true residual.
@@ -87,6 +88,31 @@ def test_cd2d_1000_roots_and_solve(env, cd2d):
     x, st = p.solve(Ad, to_dev(torch, P.b), P.m, P.tol, roots=R)
     rel = np.linalg.norm(P.b - As @ x.cpu().numpy()) / np.linalg.norm(P.b)
     assert st["converged"] == 1 and rel <= P.tol
+
+
+def test_cd2d_1000_residual_history_first_two_cycles(env, cd2d):
+    """The whole 1000 x 1000 solve with the oracle's roots on both sides: the
+    true residual and the shortcut estimate after the first restart cycle
+    (a device solve capped at one cycle), then iterations, cycles and mvps
+    of the converged solve, against the oracle's PP-GMRES."""
+    p, torch = env
+    P, As, orc, Ad = cd2d
+    R = p.Roots.from_complex(orc.roots)
+    xo, so = gmres.pp_gmres(As, orc.roots, P.b, P.m, P.tol, max_cycles=2)
+    assert len(so.true_history) >= 1
+    b = to_dev(torch, P.b)
+    _, s1 = p.solve(Ad, b, P.m, P.tol, roots=R, max_cycles=1)
+    if so.cycles > 1:
+        assert s1["converged"] == 0 and s1["cycles"] == 1
+        assert abs(s1["true_relres"] - so.true_history[0]) <= 1e-6 * so.true_history[0]
+        assert abs(s1["est_relres"] - so.history[P.m - 1]) <= 1e-6 * so.history[P.m - 1]
+    x, st = p.solve(Ad, b, P.m, P.tol, roots=R, max_cycles=2)
+    assert st["converged"] == 1 and so.converged
+    assert st["cycles"] == so.cycles
+    assert abs(st["iters"] - so.iters) <= 2
+    assert st["mvps"] - so.mvps == (st["iters"] - so.iters) * R.n_total
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
 @pytest.fixture(scope="module")
