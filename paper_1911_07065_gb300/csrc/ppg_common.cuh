@@ -133,6 +133,7 @@ struct StepArgs {
     T c1, c2, c3;
     int32_t flags;
     double* part;
+    int32_t pf_ahead;   // tiles ahead to prefetch into L2 (set by launch_step)
 };
 
 // launch one fused step; returns the number of blocks (= partial sums for

@@ -24,6 +24,8 @@
 // copied with an evict-last hint and stays resident across the roots of a
 // chain (every root reads the same A); otherwise with evict-first, so that
 // streaming A does not push the vectors out.
+#include <atomic>
+
 #include "ppg_common.cuh"
 
 namespace ppg {
@@ -46,6 +48,17 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem, uint64_t 
     asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(s),
                  "l"(gmem), "n"(BYTES), "l"(pol)
                  : "memory");
+}
+
+// Hint: bring [b, e) into L2 (16-byte granules inside the range; nothing
+// waits on it).  Both ends are rounded down to 16 bytes, which stays inside
+// the (at least 256-byte aligned) allocation that holds the range.
+__device__ __forceinline__ void prefetch_l2(const void* b, const void* e) {
+    const uintptr_t lo = (uintptr_t)b & ~(uintptr_t)15;
+    const uintptr_t hi = (uintptr_t)e & ~(uintptr_t)15;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo))
+                     : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -94,7 +107,9 @@ __device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T
     }
 }
 
-template <typename T, int OP>
+// PF: prefetch the tile one resident wave ahead into L2 (launched when the
+// matrix is not held in an L2 set-aside)
+template <typename T, int OP, bool PF>
 __global__ void __launch_bounds__(SPMV_ROWS)
 k_spmv_step(const StepArgs<T> a) {
     __shared__ T sval[SPMV_CHUNK];
@@ -110,6 +125,20 @@ k_spmv_step(const StepArgs<T> a) {
     // now; everything up to griddepcontrol.wait reads only the matrix, which
     // no step writes, so it overlaps the previous step's tail.
     asm volatile("griddepcontrol.launch_dependents;");
+    // the tile that the CTA one resident wave later stages: its nonzero
+    // range is read now, beside this tile's row pointers.  CTAs of the last
+    // wave prefetch the matrix tiles of the next step's first wave instead
+    // (a chain's next step reads the same matrix).
+    int64_t prow = row0 + (int64_t)a.pf_ahead * SPMV_ROWS;
+    const bool wrap = prow >= a.n;
+    if (wrap) prow -= (int64_t)gridDim.x * SPMV_ROWS;
+    const bool pf = PF && tid == 0 && a.pf_ahead > 0 && prow >= 0 && prow < a.n;
+    const int64_t prow1 = min(prow + SPMV_ROWS, (int64_t)a.n);
+    int32_t pk0 = 0, pk1 = 0;
+    if (pf) {
+        pk0 = __ldg(a.rowptr + prow);
+        pk1 = __ldg(a.rowptr + prow1);
+    }
     for (int i = tid; i <= nrows; i += SPMV_ROWS) srp[i] = __ldg(a.rowptr + row0 + i);
     __syncthreads();
     const int32_t k0 = srp[0];
@@ -123,8 +152,18 @@ k_spmv_step(const StepArgs<T> a) {
             cp_async<4>(scol + (k - k0), a.colind + k, pol);
         }
     }
+    if (pf) {
+        prefetch_l2(a.vals + pk0, a.vals + pk1);
+        prefetch_l2(a.colind + pk0, a.colind + pk1);
+    }
     // the vectors written by the previous step are complete and visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (pf && !wrap) {
+        prefetch_l2(a.x + prow, a.x + prow1);
+        if (a.a0) prefetch_l2(a.a0 + prow, a.a0 + prow1);
+        if (a.a1 && !(a.flags & F_PZERO)) prefetch_l2(a.a1 + prow, a.a1 + prow1);
+        if (a.a2 && (a.flags & F_FINAL)) prefetch_l2(a.a2 + prow, a.a2 + prow1);
+    }
 
     // The epilogue's row-aligned inputs do not depend on the product: load
     // them now, so their latency overlaps the staging and the gathers.
@@ -270,10 +309,52 @@ int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec) {
     return F_KEEP_A;
 }
 
+// CTAs of the root-step kernel resident at once (occupancy x SMs), per
+// device and element type
 template <typename T>
-int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s) {
-    if (a.n <= 0) return 0;
-    const int grid = spmv_grid_blocks(a.n);
+static int step_resident_ctas() {
+    static std::atomic<int> cached[16];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int occ = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_step<T, OP_P_REAL, true>,
+                                                          SPMV_ROWS, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1)
+            sms = 1;
+        cudaGetLastError();
+        v = occ * sms;
+        cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+template <typename T, bool PF>
+static cudaError_t launch_op(cudaLaunchConfig_t& cfg, int op, const StepArgs<T>& a) {
+    switch (op) {
+        case OP_SPMV: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_SPMV, PF>, a);
+        case OP_RESID: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_RESID, PF>, a);
+        case OP_PHI_REAL: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_REAL, PF>, a);
+        case OP_PHI_PAIR2: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_PAIR2, PF>, a);
+        case OP_P_REAL: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_REAL, PF>, a);
+        case OP_P_PAIR1: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR1, PF>, a);
+        case OP_P_PAIR2: return cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR2, PF>, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
+    if (a_in.n <= 0) return 0;
+    const int grid = spmv_grid_blocks(a_in.n);
+    StepArgs<T> a = a_in;
+    // prefetch ahead by one resident wave, unless the matrix is held in an
+    // L2 set-aside (measured: the prefetches then cost more than they save)
+    a.pf_ahead = (a.flags & F_KEEP_A) ? 0 : step_resident_ctas<T>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(SPMV_ROWS);
@@ -284,17 +365,9 @@ int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    switch (op) {
-        case OP_SPMV: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_SPMV>, a); break;
-        case OP_RESID: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_RESID>, a); break;
-        case OP_PHI_REAL: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_REAL>, a); break;
-        case OP_PHI_PAIR2: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_PHI_PAIR2>, a); break;
-        case OP_P_REAL: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_REAL>, a); break;
-        case OP_P_PAIR1: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR1>, a); break;
-        case OP_P_PAIR2: e = cudaLaunchKernelEx(&cfg, k_spmv_step<T, OP_P_PAIR2>, a); break;
-        default: return PPG_ERR_ARG;
-    }
+    if (op < OP_SPMV || op > OP_P_PAIR2) return PPG_ERR_ARG;
+    const cudaError_t e =
+        a.pf_ahead > 0 ? launch_op<T, true>(cfg, op, a) : launch_op<T, false>(cfg, op, a);
     ++g_launches;
     if (e != cudaSuccess) {
         set_cuda_error(e, "cudaLaunchKernelEx(k_spmv_step)");
