@@ -46,6 +46,7 @@ constexpr int OP_NOP = -2;
 constexpr int OP_AXPY_B = -1;    // the elementwise step of a degree-one plan
 constexpr int BCH = 8;           // columns per dot chunk
 constexpr int BCHUNK = 2048;     // nonzeros staged per chunk
+constexpr int BUNIT = 8;         // tiles per CTA of the batched CGS2 passes
 
 struct BStep {
     int op, flags;
@@ -217,33 +218,38 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
 }
 
 template <int NR, int NQ>
-__device__ __forceinline__ void bdot_rows(const double* const* col, const double* __restrict__ w,
-                                          int64_t base, int tid, int k, double* acc) {
+__device__ __forceinline__ void bdot_unit(const double* const* col, const double* __restrict__ w,
+                                          int t0, int t1, int tid, int k, double* acc) {
     constexpr int RP = 256 / NR;   // rows per pass
+#pragma unroll 2
+    for (int t = t0; t < t1; ++t) {
+        const int64_t base = (int64_t)t * BT;
 #pragma unroll
-    for (int p = 0; p < NR; ++p) {
-        const int64_t idx = (base + p * RP + tid / NR) * NR + k;
-        const double wv = w[idx];
+        for (int p = 0; p < NR; ++p) {
+            const int64_t idx = (base + p * RP + tid / NR) * NR + k;
+            const double wv = w[idx];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + idx), wv, acc[q]);
+            for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + idx), wv, acc[q]);
+        }
     }
 }
 
-// Partial dot products per tile: part[tile * pstr + c * NR + k] =
-// sum over the tile's rows of col_c[r, k] * w[r, k], where col_c is basis
-// column c (c < ncol) or w itself (c == ncol, with_self).  Thread t takes
-// rhs k = t % NR of rows t / NR, t / NR + 256 / NR, ...
+// Partial dot products per unit (up to BUNIT consecutive tiles of one
+// system): part[unit * pstr + c * NR + k] = sum over the unit's rows of
+// col_c[r, k] * w[r, k], where col_c is basis column c (c < ncol) or w
+// itself (c == ncol, with_self).  Thread t takes rhs k = t % NR of rows
+// t / NR, t / NR + 256 / NR, ... of every tile of the unit.
 template <int NR>
 __global__ void __launch_bounds__(256)
 k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __restrict__ w,
-       int with_self, double* part, int64_t pstr, const int32_t* __restrict__ sys_of_tile,
-       const int32_t* __restrict__ active) {
+       int with_self, double* part, int64_t pstr, const int32_t* __restrict__ unit_tile0,
+       const int32_t* __restrict__ sys_of_unit, const int32_t* __restrict__ active) {
     __shared__ double sred[8][BCH][NR];
     // stopped systems: their partial sums are never read
-    if (active && !sys_live<NR>(active, sys_of_tile[blockIdx.x])) return;
+    if (active && !sys_live<NR>(active, sys_of_unit[blockIdx.x])) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = tid % NR;
-    constexpr int RP = 256 / NR;   // rows per pass
+    const int t0 = unit_tile0[blockIdx.x], t1 = unit_tile0[blockIdx.x + 1];
     const int c0 = blockIdx.y * BCH;
     const int nvals = ncol + (with_self ? 1 : 0);
     const int nq = min(BCH, nvals - c0);
@@ -256,16 +262,15 @@ k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __rest
     double acc[BCH];
 #pragma unroll
     for (int q = 0; q < BCH; ++q) acc[q] = 0.0;
-    const int64_t base = (int64_t)blockIdx.x * BT;
     switch (nq) {   // compile-time widths: no FP64 FMA for a missing column
-        case 8: bdot_rows<NR, 8>(col, w, base, tid, k, acc); break;
-        case 7: bdot_rows<NR, 7>(col, w, base, tid, k, acc); break;
-        case 6: bdot_rows<NR, 6>(col, w, base, tid, k, acc); break;
-        case 5: bdot_rows<NR, 5>(col, w, base, tid, k, acc); break;
-        case 4: bdot_rows<NR, 4>(col, w, base, tid, k, acc); break;
-        case 3: bdot_rows<NR, 3>(col, w, base, tid, k, acc); break;
-        case 2: bdot_rows<NR, 2>(col, w, base, tid, k, acc); break;
-        default: bdot_rows<NR, 1>(col, w, base, tid, k, acc); break;
+        case 8: bdot_unit<NR, 8>(col, w, t0, t1, tid, k, acc); break;
+        case 7: bdot_unit<NR, 7>(col, w, t0, t1, tid, k, acc); break;
+        case 6: bdot_unit<NR, 6>(col, w, t0, t1, tid, k, acc); break;
+        case 5: bdot_unit<NR, 5>(col, w, t0, t1, tid, k, acc); break;
+        case 4: bdot_unit<NR, 4>(col, w, t0, t1, tid, k, acc); break;
+        case 3: bdot_unit<NR, 3>(col, w, t0, t1, tid, k, acc); break;
+        case 2: bdot_unit<NR, 2>(col, w, t0, t1, tid, k, acc); break;
+        default: bdot_unit<NR, 1>(col, w, t0, t1, tid, k, acc); break;
     }
     // sum over the lanes that share k
 #pragma unroll
@@ -304,39 +309,43 @@ __global__ void k_bsegsum(const double* part, int64_t pstr, int nvals, int NR,
     }
 }
 
-// w[r, k] -= sum_c V_c[r, k] h[c, solve(r, k)]; with_norm: per-tile
-// partial sums of the new w[r, k]^2 in part[tile * NR + k].
+// w[r, k] -= sum_c V_c[r, k] h[c, solve(r, k)] over the rows of one unit
+// per CTA; with_norm: per-unit partial sums of the new w[r, k]^2 in
+// part[unit * NR + k].
 template <int NR>
 __global__ void __launch_bounds__(256)
 k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
-       const double* __restrict__ h, int nsolve, const int32_t* __restrict__ sys_of_tile,
-       int with_norm, double* part, const int32_t* __restrict__ active) {
+       const double* __restrict__ h, int nsolve, const int32_t* __restrict__ unit_tile0,
+       const int32_t* __restrict__ sys_of_unit, int with_norm, double* part,
+       const int32_t* __restrict__ active) {
     __shared__ double sh[ORTHO_MAXC][NR];
     __shared__ double sred[8][NR];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = tid % NR;
     constexpr int RP = 256 / NR;
-    const int64_t tile = blockIdx.x;
-    const int s = sys_of_tile[tile];
+    const int s = sys_of_unit[blockIdx.x];
     if (active && !sys_live<NR>(active, s)) return;
+    const int t0 = unit_tile0[blockIdx.x], t1 = unit_tile0[blockIdx.x + 1];
     for (int e = tid; e < ncol * NR; e += 256)
         sh[e / NR][e % NR] = h[(size_t)(e / NR) * nsolve + s * NR + e % NR];
     __syncthreads();
     double nacc = 0.0;
-    const int64_t base = tile * BT;
+    for (int t = t0; t < t1; ++t) {
+        const int64_t base = (int64_t)t * BT;
 #pragma unroll
-    for (int p = 0; p < NR; ++p) {
-        const int64_t idx = (base + p * RP + tid / NR) * NR + k;
-        double s0 = 0.0, s1 = 0.0;
-        int c = 0;
-        for (; c + 1 < ncol; c += 2) {
-            s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
-            s1 = fma(__ldcs(V + (c + 1) * ldV + idx), sh[c + 1][k], s1);
+        for (int p = 0; p < NR; ++p) {
+            const int64_t idx = (base + p * RP + tid / NR) * NR + k;
+            double s0 = 0.0, s1 = 0.0;
+            int c = 0;
+            for (; c + 1 < ncol; c += 2) {
+                s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
+                s1 = fma(__ldcs(V + (c + 1) * ldV + idx), sh[c + 1][k], s1);
+            }
+            if (c < ncol) s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
+            const double wn = w[idx] - (s0 + s1);
+            w[idx] = wn;
+            nacc = fma(wn, wn, nacc);
         }
-        if (c < ncol) s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
-        const double wn = w[idx] - (s0 + s1);
-        w[idx] = wn;
-        nacc = fma(wn, wn, nacc);
     }
     if (!with_norm) return;
     for (int off = NR; off < 32; off <<= 1) nacc += __shfl_xor_sync(0xffffffffu, nacc, off);
@@ -345,7 +354,7 @@ k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
     if (tid < NR) {
         double t = 0.0;
         for (int ww = 0; ww < 8; ++ww) t += sred[ww][tid];
-        part[(size_t)tile * NR + tid] = t;
+        part[(size_t)blockIdx.x * NR + tid] = t;
     }
 }
 
@@ -564,8 +573,14 @@ struct Batch {
     std::vector<int64_t> off;      // row offset per system
     std::vector<int32_t> n;        // rows per system
     std::vector<int32_t> tile0_h;  // first tile per system, nsys + 1
+    // units of the CGS2 passes: up to BUNIT consecutive tiles of one system
+    int64_t nunits = 0;
+    std::vector<int32_t> unit_tile0_h;   // first tile per unit, nunits + 1
+    std::vector<int32_t> unit0_h;        // first unit per system, nsys + 1
+    std::vector<int32_t> sys_of_unit_h;  // nunits
     // device
-    int32_t *rowptr, *colind, *sys_of_tile, *tile0, *cta0;
+    int32_t *rowptr, *colind, *sys_of_tile, *cta0;
+    int32_t *unit_tile0, *unit0, *sys_of_unit;
     double* v64;
     float* v32;
     int rows_per_cta = 256;
@@ -621,17 +636,18 @@ int32_t cgs2_batch(const Batch& B, Work& W, int j, double* wcol, int with_self, 
         const int self = (pass == 0) ? with_self : 0;
         const int nvals = ncol + self;
         double* h = pass == 0 ? W.h1 : W.h2;
-        k_bdot<NR><<<dim3((unsigned)B.ntiles, (nvals + BCH - 1) / BCH), 256, 0, s>>>(
-            W.V, ldV, ncol, wcol, self, W.part, pstr, B.sys_of_tile, active);
+        k_bdot<NR><<<dim3((unsigned)B.nunits, (nvals + BCH - 1) / BCH), 256, 0, s>>>(
+            W.V, ldV, ncol, wcol, self, W.part, pstr, B.unit_tile0, B.sys_of_unit, active);
         BCHECK("k_bdot");
-        k_bsegsum<<<dim3(B.nsys, (nvals + 7) / 8), 256, 0, s>>>(W.part, pstr, nvals, NR, B.tile0,
+        k_bsegsum<<<dim3(B.nsys, (nvals + 7) / 8), 256, 0, s>>>(W.part, pstr, nvals, NR, B.unit0,
                                                                 B.nsys, h);
         BCHECK("k_bsegsum");
-        k_bsub<NR><<<(unsigned)B.ntiles, 256, 0, s>>>(W.V, ldV, ncol, wcol, h, nsolve,
-                                                      B.sys_of_tile, pass == 1, W.part, active);
+        k_bsub<NR><<<(unsigned)B.nunits, 256, 0, s>>>(W.V, ldV, ncol, wcol, h, nsolve,
+                                                      B.unit_tile0, B.sys_of_unit, pass == 1,
+                                                      W.part, active);
         BCHECK("k_bsub");
     }
-    k_bsegsum<<<dim3(B.nsys, 1), 256, 0, s>>>(W.part, NR, 1, NR, B.tile0, B.nsys, W.nrm);
+    k_bsegsum<<<dim3(B.nsys, 1), 256, 0, s>>>(W.part, NR, 1, NR, B.unit0, B.nsys, W.nrm);
     BCHECK("k_bsegsum");
     return PPG_OK;
 }
@@ -767,6 +783,19 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     B.N = N;
     B.nnz = nnz;
     B.ntiles = N / BT;
+    B.unit_tile0_h.clear();
+    B.sys_of_unit_h.clear();
+    B.unit0_h.assign(nsys + 1, 0);
+    for (int i = 0; i < nsys; ++i) {
+        B.unit0_h[i] = (int32_t)B.unit_tile0_h.size();
+        for (int32_t t = B.tile0_h[i]; t < B.tile0_h[i + 1]; t += BUNIT) {
+            B.unit_tile0_h.push_back(t);
+            B.sys_of_unit_h.push_back(i);
+        }
+    }
+    B.unit0_h[nsys] = (int32_t)B.unit_tile0_h.size();
+    B.nunits = (int64_t)B.unit_tile0_h.size();
+    B.unit_tile0_h.push_back((int32_t)B.ntiles);
     const int nsolve = nsys * NR;
     const int64_t ldV = N * NR;
 
@@ -779,8 +808,10 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     ar.add(&B.v64, (size_t)nnz);
     ar.add(&B.v32, (size_t)nnz);
     ar.add(&B.sys_of_tile, (size_t)B.ntiles);
-    ar.add(&B.tile0, (size_t)nsys + 1);
     ar.add(&B.cta0, (size_t)nsys + 1);
+    ar.add(&B.unit_tile0, (size_t)B.nunits + 1);
+    ar.add(&B.unit0, (size_t)nsys + 1);
+    ar.add(&B.sys_of_unit, (size_t)std::max<int64_t>(B.nunits, 1));
     ar.add(&W.V, (size_t)(mk + 1) * ldV);
     ar.add(&W.Z, (size_t)m * ldV);
     ar.add(&W.fa, (size_t)ldV);
@@ -822,8 +853,13 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
         for (int t = B.tile0_h[i]; t < B.tile0_h[i + 1]; ++t) sot[t] = i;
     PPG_CUDA(cudaMemcpyAsync(B.sys_of_tile, sot.data(), sizeof(int32_t) * B.ntiles,
                              cudaMemcpyHostToDevice, s));
-    PPG_CUDA(cudaMemcpyAsync(B.tile0, B.tile0_h.data(), sizeof(int32_t) * (nsys + 1),
+    PPG_CUDA(cudaMemcpyAsync(B.unit_tile0, B.unit_tile0_h.data(),
+                             sizeof(int32_t) * (B.nunits + 1), cudaMemcpyHostToDevice, s));
+    PPG_CUDA(cudaMemcpyAsync(B.unit0, B.unit0_h.data(), sizeof(int32_t) * (nsys + 1),
                              cudaMemcpyHostToDevice, s));
+    if (B.nunits > 0)
+        PPG_CUDA(cudaMemcpyAsync(B.sys_of_unit, B.sys_of_unit_h.data(),
+                                 sizeof(int32_t) * B.nunits, cudaMemcpyHostToDevice, s));
     int64_t nz_off = 0;
     for (int i = 0; i < nsys; ++i) {
         const int32_t np = B.tile0_h[i + 1] * BT - B.tile0_h[i] * BT;
@@ -857,10 +893,11 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
             BCHECK("k_pack_vec");
         }
         // ||v0|| per system, V_0 = v0 / ||v0||
-        k_bdot<1><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, N, 0, W.V, 1, W.part, W.pstr,
-                                                               B.sys_of_tile, nullptr);
+        k_bdot<1><<<dim3((unsigned)B.nunits, 1), 256, 0, s>>>(W.V, N, 0, W.V, 1, W.part, W.pstr,
+                                                               B.unit_tile0, B.sys_of_unit,
+                                                               nullptr);
         BCHECK("k_bdot");
-        k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, 1, B.tile0, nsys, W.nrm);
+        k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, 1, B.unit0, nsys, W.nrm);
         BCHECK("k_bsegsum");
         BState bst = W.st;
         PPG_CUDA(cudaMemsetAsync(bst.brk, 0xff, sizeof(int32_t) * nsys, s));
@@ -961,10 +998,10 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     }
     PPG_CUDA(cudaMemsetAsync(W.X, 0, sizeof(double) * ldV, s));
     PPG_CUDA(cudaMemcpyAsync(W.V, W.Bp, sizeof(double) * ldV, cudaMemcpyDeviceToDevice, s));
-    k_bdot<NR><<<dim3((unsigned)B.ntiles, 1), 256, 0, s>>>(W.V, ldV, 0, W.V, 1, W.part, W.pstr,
-                                                           B.sys_of_tile, nullptr);
+    k_bdot<NR><<<dim3((unsigned)B.nunits, 1), 256, 0, s>>>(W.V, ldV, 0, W.V, 1, W.part, W.pstr,
+                                                           B.unit_tile0, B.sys_of_unit, nullptr);
     BCHECK("k_bdot");
-    k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, NR, B.tile0, nsys, W.nrm);
+    k_bsegsum<<<dim3(nsys, 1), 256, 0, s>>>(W.part, W.pstr, 1, NR, B.unit0, nsys, W.nrm);
     BCHECK("k_bsegsum");
     k_bcycle<<<sgn, 128, 0, s>>>(W.st, nsolve, m, W.nrm, tol, 1);
     BCHECK("k_bcycle");
