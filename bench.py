@@ -565,6 +565,7 @@ def run_profile_case(name):
     ``arnoldi_cd2d_2000``: the degree-30 polynomial construction on it (CGS2);
     ``phi_cd2d_1000``: two applications of the benchmark's own polynomial;
     ``batched_64x4``: one call of the batching form on its full workload;
+    ``batched_16x4``: the same with its first 16 systems;
     ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix."""
     import numpy as np
     import torch
@@ -588,9 +589,11 @@ def run_profile_case(name):
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
         y = ppg.apply_phi(Ad, R, v)
         y = ppg.apply_phi(Ad, R, y)
-    elif name == "batched_64x4":
-        # the batching workload: 64 systems x 4 right-hand sides, one call
-        probs = synth.batch_problem(nsys=64, seed=104)
+    elif name in ("batched_64x4", "batched_16x4"):
+        # the batching workload: 64 systems x 4 right-hand sides, one call;
+        # batched_16x4: its first 16 systems (same recipe; about 2 GB on the
+        # device, for full ncu captures)
+        probs = synth.batch_problem(nsys=64 if name == "batched_64x4" else 16, seed=104)
         dA = [ppg.CSR.from_host(A.rowptr, A.colind, A.vals) for A, _, _ in probs]
         dB = [torch.from_numpy(np.ascontiguousarray(B)).cuda() for _, B, _ in probs]
         dv = [torch.from_numpy(v).cuda() for _, _, v in probs]
