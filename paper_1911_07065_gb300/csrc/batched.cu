@@ -1113,7 +1113,7 @@ extern "C" int32_t ppg_solve_batched(int32_t nsys, const ppg_csr* As, int32_t nr
                                      ppg_stats* stats, double* relres_out, int32_t* iters_out,
                                      void* stream) {
     if (nsys < 1 || !As || !B || !X || !v0 || (nrhs != 1 && nrhs != 4)) return PPG_ERR_ARG;
-    if (d < 2 || m < 1 || m + 1 > ORTHO_MAXC || d + 1 > ORTHO_MAXC || !(tol > 0.0))
+    if (d < 1 || m < 1 || m + 1 > ORTHO_MAXC || d + 1 > ORTHO_MAXC || !(tol > 0.0))
         return PPG_ERR_ARG;
     for (int i = 0; i < nsys; ++i) {
         const ppg_csr& A = As[i];

@@ -1,0 +1,118 @@
+"""Edge cases of the device path (run with -m gpu).
+
+* CSR arrays that do not start on a 16-byte boundary (views one element into
+  a buffer): the root-step kernels then stage values and column indices one
+  element at a time instead of in 16-byte granules.  Staging only moves data,
+  so y = A x, p(A) v and phi(A) v must be bit-identical to the aligned run,
+  in FP64 and FP32, including matrices with rows longer than one staging
+  chunk and empty rows.
+* The batching form with a degree-one polynomial (p(A) = 1/theta, the
+  elementwise step) against the oracle's FGMRES with the same root.
+* The batching form on systems so small that the GMRES(d) construction
+  breaks down (n < d): per-system degrees differ, the shorter step tables are
+  padded with no-ops; roots, iteration counts and solutions against the
+  oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gmres, poly
+
+from gpu_util import dev_csr, ppg_or_skip, random_csr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ROOTS = np.array([4.0, 3 + 1j, 3 - 1j, 2.5, 2 + 0.5j, 2 - 0.5j, 3.3], dtype=complex)
+
+
+@pytest.fixture(scope="module")
+def env():
+    return ppg_or_skip()
+
+
+def _unaligned(torch, t, offset=1):
+    """The same values in a view that starts `offset` elements into a fresh
+    buffer (4 or 8 bytes past a 256-byte aligned allocation)."""
+    buf = torch.empty(t.numel() + offset, dtype=t.dtype, device=t.device)
+    view = buf[offset:]
+    view.copy_(t)
+    assert view.data_ptr() % 16 != 0
+    return view
+
+
+def _matrices():
+    yield "cd2d_37", synth.cd2d(37, 0.7)
+    yield "cd3d_13", synth.cd3d(13, (0.8, 0.4, 0.2))
+    yield "random_long_empty", random_csr(3001, 1, long_rows={5: 2500, 700: 4100},
+                                          empty_rows={17, 1000, 3000})
+
+
+@pytest.mark.parametrize("which", ["vals", "colind", "both"])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("mname,A", list(_matrices()))
+def test_unaligned_csr_arrays_bitwise(env, mname, A, dtype, which):
+    p, torch = env
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    Ad = dev_csr(p, torch, A, dtype=tdt)
+    ci = _unaligned(torch, Ad.colind) if which in ("colind", "both") else Ad.colind
+    vv = _unaligned(torch, Ad.vals) if which in ("vals", "both") else Ad.vals
+    Au = p.CSR(Ad.rowptr, ci, vv)
+    R = p.Roots.from_complex(ROOTS)
+    v = to_dev(torch, np.random.default_rng(11).standard_normal(A.n), tdt)
+    assert torch.equal(p.spmv(Ad, v), p.spmv(Au, v))
+    assert torch.equal(p.apply_poly(Ad, R, v), p.apply_poly(Au, R, v))
+    assert torch.equal(p.apply_phi(Ad, R, v), p.apply_phi(Au, R, v))
+
+
+def _batched(p, torch, probs, d, m, tol):
+    As = [dev_csr(p, torch, A) for A, _, _ in probs]
+    Bs = [to_dev(torch, np.ascontiguousarray(B)) for _, B, _ in probs]
+    v0s = [to_dev(torch, v0) for _, _, v0 in probs]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        Xs, info = p.solve_batched(As, Bs, v0s, d, m, tol)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    return [x.cpu().numpy() for x in Xs], info
+
+
+def _check_against_oracle(probs, Xs, info, d, m, tol):
+    for s, (A, B, v0) in enumerate(probs):
+        As = A.to_scipy()
+        orc = poly.build_poly(As, d, v0)
+        R = info["roots"][s]
+        assert R.n_total == orc.roots.size, (s, A.n, R.n_total, orc.roots.size)
+        got = R.complex()
+        for t in orc.roots:
+            assert np.min(np.abs(got - t)) <= 1e-8 * abs(t)
+        for k in range(B.shape[0]):
+            rel = np.linalg.norm(B[k] - As @ Xs[s][k]) / np.linalg.norm(B[k])
+            assert rel <= tol, (s, k, rel)
+            xo, so = gmres.fgmres_p(As, got, B[k], m, tol, inner="f32")
+            assert abs(int(info["iters"][s, k]) - so.iters) <= 2, (s, k)
+            assert np.linalg.norm(Xs[s][k] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_batched_degree_one_polynomial(env):
+    p, torch = env
+    probs = synth.batch_problem(nsys=5, seed=21, side_lo=6, side_hi=12, nrhs=4)
+    d, m, tol = 1, 20, 1e-10
+    Xs, info = _batched(p, torch, probs, d, m, tol)
+    assert info["status"] == 0
+    assert all(info["roots"][s].n_total == 1 for s in range(len(probs)))
+    _check_against_oracle(probs, Xs, info, d, m, tol)
+
+
+def test_batched_mixed_degrees_with_breakdown(env):
+    p, torch = env
+    # sides 2..5 (n = 4..25) with d = 12: the smallest systems exhaust their
+    # Krylov space before step d, so their polynomials are shorter
+    probs = synth.batch_problem(nsys=8, seed=22, side_lo=2, side_hi=5, nrhs=4)
+    d, m, tol = 12, 20, 1e-10
+    Xs, info = _batched(p, torch, probs, d, m, tol)
+    assert info["status"] == 0
+    degrees = {info["roots"][s].n_orig for s in range(len(probs))}
+    assert len(degrees) > 1, degrees
+    _check_against_oracle(probs, Xs, info, d, m, tol)
