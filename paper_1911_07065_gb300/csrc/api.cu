@@ -117,12 +117,27 @@ static T* mbuf(const Buffers& b, int id) {
 }
 
 template <typename T>
+static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const int32_t* rowptr,
+                         const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
+                         const Buffers& bufs, cudaStream_t s, double* bytes_out);
+
+template <typename T>
 int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr, const int32_t* colind,
                  const T* vals, int32_t n, int64_t nnz, const Buffers& bufs, cudaStream_t s,
                  double* bytes_out) {
+    return run_steps<T>(plan, 0, (int)plan.size(), rowptr, colind, vals, n, nnz, bufs, s,
+                        bytes_out);
+}
+
+// steps [i0, i1) of a plan, in order
+template <typename T>
+static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const int32_t* rowptr,
+                         const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
+                         const Buffers& bufs, cudaStream_t s, double* bytes_out) {
     double bytes = 0.0;
     const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3);
-    for (const Step& st : plan) {
+    for (int i = i0; i < i1; ++i) {
+        const Step& st = plan[(size_t)i];
         if (st.op == OP_AXPY) {
             const bool pz = st.flags & F_PZERO;
             PPG_TRY(launch_axpby<T>((T)st.c1, cbuf<T>(bufs, st.x), pz ? T(0) : T(1),
@@ -425,9 +440,22 @@ static int32_t run_solve(SolveCore& c) {
     PPG_CUDA(cudaMemsetAsync(c.ows.counter, 0, 4 * sizeof(unsigned), s));
     PPG_CUDA(cudaMemsetAsync(c.gs.scal, 0, 8 * sizeof(double), s));
 
-    EventPair ev_poly, ev_orth;
-    PPG_TRY(ev_poly.init(c.opts.timing != 0));
-    PPG_TRY(ev_orth.init(c.opts.timing != 0));
+    // timers of two consecutive Arnoldi steps (the look-ahead records the
+    // next step's before the current one is read) and of the restart update
+    EventPair ev_poly[2], ev_orth[2], ev_restart;
+    for (int i = 0; i < 2; ++i) {
+        PPG_TRY(ev_poly[i].init(c.opts.timing != 0));
+        PPG_TRY(ev_orth[i].init(c.opts.timing != 0));
+    }
+    PPG_TRY(ev_restart.init(c.opts.timing != 0));
+    // marks the copy of a step's residual estimate: the host waits for it,
+    // not for the look-ahead enqueued behind it
+    struct ReadyEvent {
+        cudaEvent_t e = nullptr;
+        ~ReadyEvent() { if (e) cudaEventDestroy(e); }
+    } ready;
+    PPG_CUDA(cudaEventCreateWithFlags(&ready.e, cudaEventDisableTiming));
+    cudaEvent_t ev_ready = ready.e;
 
     c.st = ppg_stats{};
     double* scal_h = nullptr;
@@ -489,84 +517,118 @@ static int32_t run_solve(SolveCore& c) {
     phib.ptr[B_C] = c.vc;
     Buffers pb{};
 
+    // One Arnoldi step: the operator chain (phi(A) v_j by Algorithm 1; in the
+    // flexible form z_j = p(A) v_j by Algorithm 3 in FP32 and w = A z_j; plain
+    // GMRES: w = A v_j), CGS2, the Givens update, and the copy of the
+    // residual estimate to the host.
+    //
+    // Look-ahead: before the host waits for step j's estimate, the scaling of
+    // v_{j+1} and the first `nahead` chain kernels of step j + 1 are already
+    // enqueued, so the GPU stays busy across the host round trip.  If the
+    // cycle stops at step j they have written only work vectors (the prefix
+    // never includes a chain's last step) and basis column j + 1, which the
+    // update does not read.
+    constexpr int kLookahead = 2;
+    const std::vector<Step>* chain = pp ? (c.flex ? &c.p_plan : &c.phi_plan) : nullptr;
+    const int nahead = chain ? std::max(0, std::min(kLookahead, (int)chain->size() - 1)) : 0;
+    auto chain_steps = [&](int j, int i0, int i1, double* by) -> int32_t {
+        if (c.flex) {
+            Buffers fb{};
+            fb.ptr[B_IN] = c.v32;
+            fb.ptr[B_P] = c.Z32 + (size_t)j * c.ldv;
+            fb.ptr[B_A] = c.fa;
+            fb.ptr[B_B] = c.fb;
+            fb.ptr[B_C] = c.fc;
+            return run_steps<float>(c.p_plan, i0, i1, c.A32->rowptr, c.A32->colind,
+                                    (const float*)c.A32->vals, n, nnz, fb, s, by);
+        }
+        phib.ptr[B_IN] = c.V + (size_t)j * c.ldv;
+        phib.ptr[B_OUT] = c.V + (size_t)(j + 1) * c.ldv;
+        return run_steps<double>(c.phi_plan, i0, i1, c.A64->rowptr, c.A64->colind,
+                                 (const double*)c.A64->vals, n, nnz, phib, s, by);
+    };
+    // start of step j: the FP32 cast of v_j (flexible form), the chain timer
+    // (root steps only, not the cast) and chain steps [0, upto)
+    auto begin_step = [&](int j, int e, int upto, double* by) -> int32_t {
+        *by = 0.0;
+        if (c.flex) PPG_TRY(launch_cast_f64_f32(c.V + (size_t)j * c.ldv, c.v32, n, s));
+        ev_poly[e].start(s);
+        if (chain && upto > 0) PPG_TRY(chain_steps(j, 0, upto, by));
+        return PPG_OK;
+    };
+    // the rest of step j from chain step `from` on
+    auto finish_step = [&](int j, int e, int from, double* by) -> int32_t {
+        double* vj = c.V + (size_t)j * c.ldv;
+        double* w = c.V + (size_t)(j + 1) * c.ldv;
+        StepArgs<double> a{};
+        a.rowptr = c.A64->rowptr;
+        a.colind = c.A64->colind;
+        a.vals = (const double*)c.A64->vals;
+        a.n = n;
+        a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
+        a.o0 = w;
+        if (c.flex) {
+            float* zj = c.Z32 + (size_t)j * c.ldv;
+            if (pp) {
+                double b2 = 0;
+                PPG_TRY(chain_steps(j, from, (int)chain->size(), &b2));
+                *by += b2;
+            } else {
+                PPG_CUDA(cudaMemcpyAsync(zj, c.v32, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                         s));
+            }
+            ev_poly[e].stop(s);
+            PPG_TRY(launch_cast_f32_f64(zj, c.u, n, s));
+            a.x = c.u;
+            const int32_t g = launch_step<double>(OP_SPMV, a, s);
+            if (g < 0) return g;
+        } else if (pp) {
+            double b2 = 0;
+            PPG_TRY(chain_steps(j, from, (int)chain->size(), &b2));
+            *by += b2;
+            ev_poly[e].stop(s);
+        } else {
+            a.x = vj;
+            const int32_t g = launch_step<double>(OP_SPMV, a, s);
+            if (g < 0) return g;
+            ev_poly[e].stop(s);
+            *by = step_bytes(OP_SPMV, 0, n, nnz, 8);
+        }
+        PPG_TRY(cgs2_column(c, j, w, false, &ev_orth[e]));
+        PPG_TRY(launch_finish_column(c.gs, ldh, j, c.ows.h1, c.ows.h2, c.ows.nrm, true, bnorm,
+                                     0.0, s));
+        ev_orth[e].stop(s);
+        PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s));
+        return PPG_OK;
+    };
+
     const int max_cycles = c.opts.max_cycles > 0 ? c.opts.max_cycles : 10000;
     for (int cyc = 0; cyc < max_cycles && !converged; ++cyc) {
         c.st.cycles += 1;
         PPG_TRY(launch_scale(c.V, c.V, n, c.gs.scal + 4, s));
         int k = 0;
+        int from = 0;        // chain steps of step j already enqueued
+        double by_cur = 0;   // their algorithmic bytes
+        PPG_TRY(begin_step(0, 0, 0, &by_cur));
         for (int j = 0; j < m; ++j) {
-            double* vj = c.V + (size_t)j * c.ldv;
+            const int e = j & 1;
             double* w = c.V + (size_t)(j + 1) * c.ldv;
-            // the polynomial timer covers the root steps only, not the cast
-            if (c.flex) PPG_TRY(launch_cast_f64_f32(vj, c.v32, n, s));
-            ev_poly.start(s);
-            if (c.flex) {
-                // z_j = p(A) v_j in FP32, then w = A64 z_j
-                float* zj = c.Z32 + (size_t)j * c.ldv;
-                if (pp) {
-                    Buffers fb{};
-                    fb.ptr[B_IN] = c.v32;
-                    fb.ptr[B_P] = zj;
-                    fb.ptr[B_A] = c.fa;
-                    fb.ptr[B_B] = c.fb;
-                    fb.ptr[B_C] = c.fc;
-                    double by = 0;
-                    PPG_TRY(run_plan<float>(c.p_plan, c.A32->rowptr, c.A32->colind,
-                                            (const float*)c.A32->vals, n, nnz, fb, s, &by));
-                    c.st.poly_bytes += by;
-                    c.st.poly_launches += (int64_t)c.p_plan.size();
-                } else {
-                    PPG_CUDA(cudaMemcpyAsync(zj, c.v32, sizeof(float) * n,
-                                             cudaMemcpyDeviceToDevice, s));
-                }
-                ev_poly.stop(s);
-                PPG_TRY(launch_cast_f32_f64(zj, c.u, n, s));
-                StepArgs<double> a{};
-                a.rowptr = c.A64->rowptr;
-                a.colind = c.A64->colind;
-                a.vals = (const double*)c.A64->vals;
-                a.n = n;
-                a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
-                a.x = c.u;
-                a.o0 = w;
-                int32_t g = launch_step<double>(OP_SPMV, a, s);
-                if (g < 0) return g;
-                c.st.mvps += d;   // d-1 in p(A) v_j, one for A z_j
-            } else if (pp) {
-                phib.ptr[B_IN] = vj;
-                phib.ptr[B_OUT] = w;
-                double by = 0;
-                PPG_TRY(run_plan<double>(c.phi_plan, c.A64->rowptr, c.A64->colind,
-                                         (const double*)c.A64->vals, n, nnz, phib, s, &by));
-                ev_poly.stop(s);
-                c.st.poly_bytes += by;
-                c.st.poly_launches += (int64_t)c.phi_plan.size();
-                c.st.mvps += d;
-            } else {
-                StepArgs<double> a{};
-                a.rowptr = c.A64->rowptr;
-                a.colind = c.A64->colind;
-                a.vals = (const double*)c.A64->vals;
-                a.n = n;
-                a.flags = keep_a_flag(a.n, c.A64->nnz, 8, 3);
-                a.x = vj;
-                a.o0 = w;
-                int32_t g = launch_step<double>(OP_SPMV, a, s);
-                if (g < 0) return g;
-                ev_poly.stop(s);
-                c.st.poly_bytes += step_bytes(OP_SPMV, 0, n, nnz, 8);
-                c.st.poly_launches += 1;
-                c.st.mvps += 1;
+            PPG_TRY(finish_step(j, e, from, &by_cur));
+            PPG_CUDA(cudaEventRecord(ev_ready, s));
+            const double by_step = by_cur;
+            from = 0;
+            if (j + 1 < m) {   // look-ahead into step j + 1
+                PPG_TRY(launch_scale(w, w, n, c.gs.scal + 2, s));
+                PPG_TRY(begin_step(j + 1, e ^ 1, nahead, &by_cur));
+                from = nahead;
             }
-            PPG_TRY(cgs2_column(c, j, w, false, &ev_orth));
-            PPG_TRY(launch_finish_column(c.gs, ldh, j, c.ows.h1, c.ows.h2, c.ows.nrm, true,
-                                         bnorm, 0.0, s));
-            ev_orth.stop(s);
-            PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 4 * sizeof(double),
-                                     cudaMemcpyDeviceToHost, s));
-            PPG_CUDA(cudaStreamSynchronize(s));
-            c.st.poly_ms += ev_poly.ms();
-            c.st.ortho_ms += ev_orth.ms();
+            PPG_CUDA(cudaEventSynchronize(ev_ready));
+            c.st.poly_ms += ev_poly[e].ms();
+            c.st.ortho_ms += ev_orth[e].ms();
+            c.st.poly_bytes += by_step;
+            c.st.poly_launches += chain ? (int64_t)chain->size() : (c.flex ? 0 : 1);
+            c.st.mvps += pp ? d : 1;   // flexible form: d-1 in p(A) v_j, one for A z_j
             c.st.iters += 1;
             c.st.dots += 2 * (j + 1) + 1;
             k = j + 1;
@@ -575,7 +637,6 @@ static int32_t run_solve(SolveCore& c) {
             c.st.est_relres = est;
             if (!std::isfinite(est) || !std::isfinite(hn)) return PPG_ERR_NONFINITE;
             if (est <= c.tol || hn == 0.0) break;
-            if (j + 1 < m) PPG_TRY(launch_scale(w, w, n, c.gs.scal + 2, s));
         }
         PPG_TRY(launch_backsolve(c.gs, ldh, k, s));
         if (c.flex) {
@@ -588,10 +649,10 @@ static int32_t run_solve(SolveCore& c) {
             pb.ptr[B_B] = c.vb;
             pb.ptr[B_C] = c.vc;
             double by = 0;
-            ev_poly.start(s);
+            ev_restart.start(s);
             PPG_TRY(run_plan<double>(c.p_plan, c.A64->rowptr, c.A64->colind,
                                      (const double*)c.A64->vals, n, nnz, pb, s, &by));
-            ev_poly.stop(s);
+            ev_restart.stop(s);
             c.st.poly_bytes += by;
             c.st.poly_launches += (int64_t)c.p_plan.size();
             c.st.mvps += d - 1;
@@ -616,7 +677,7 @@ static int32_t run_solve(SolveCore& c) {
         c.st.dots += 1;
         PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
         PPG_CUDA(cudaStreamSynchronize(s));
-        if (pp && !c.flex) c.st.poly_ms += ev_poly.ms();
+        if (pp && !c.flex) c.st.poly_ms += ev_restart.ms();
         beta = scal_h[3];
         if (!std::isfinite(beta)) return PPG_ERR_NONFINITE;
         c.st.true_relres = beta / bnorm;

@@ -450,16 +450,21 @@ __global__ void k_bscale(double* w, const double* scale, const int32_t* sys_of_t
 }
 
 __global__ void k_bbacksolve(BState st, int nsolve, int ldh, int m) {
-    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sv >= nsolve) return;
+    // one warp per solve: row i from the bottom up, the lanes sharing the
+    // sum over the solved entries c > i, lane 0 dividing
+    const int sv = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (sv >= nsolve) return;   // uniform over the warp
     const int k = st.ksteps[sv];
     const double* R = st.R + (size_t)sv * ldh * m;
     const double* g = st.g + (size_t)sv * (m + 1);
     double* y = st.y + (size_t)sv * m;
     for (int i = k - 1; i >= 0; --i) {
-        double s = g[i];
-        for (int c = i + 1; c < k; ++c) s -= R[(size_t)c * ldh + i] * y[c];
-        y[i] = s / R[(size_t)i * ldh + i];
+        double part = 0.0;
+        for (int c = i + 1 + lane; c < k; c += 32) part = fma(R[(size_t)c * ldh + i], y[c], part);
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        if (lane == 0) y[i] = (g[i] - part) / R[(size_t)i * ldh + i];
+        __syncwarp();
     }
 }
 
@@ -730,7 +735,8 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
         k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(w, W.st.inv, B.sys_of_tile, total);
         BCHECK("k_bscale");
     }
-    k_bbacksolve<<<sg, 128, 0, s>>>(W.st, nsolve, B.ldh, B.m);
+    k_bbacksolve<<<(unsigned)(((int64_t)nsolve * 32 + 127) / 128), 128, 0, s>>>(W.st, nsolve, B.ldh,
+                                                                          B.m);
     BCHECK("k_bbacksolve");
     k_bzy<NR><<<elem_grid(total), 256, 0, s>>>(W.Z, ldV, W.X, W.st, B.sys_of_tile, B.m, total);
     BCHECK("k_bzy");

@@ -353,18 +353,38 @@ int32_t launch_finish_column(const GmresState& st, int ldh, int j, const double*
     return check_launch("k_finish_column");
 }
 
-// y = R^{-1} g (k x k upper triangular), one thread
-__global__ void k_backsolve(GmresState st, int ldh, int k) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// y = R^{-1} g (k x k upper triangular; R[i][c] at R[c * ldh + i]).  The
+// CTA stages R in shared memory (k <= BS_MAXK), then one warp solves from
+// the bottom row up: for row i the lanes share the sum over the solved
+// entries c > i, lane 0 divides.  Larger k reads R from global memory.
+constexpr int BS_MAXK = 64;
+
+__global__ void __launch_bounds__(256) k_backsolve(GmresState st, int ldh, int k) {
+    __shared__ double sR[BS_MAXK * BS_MAXK];
+    __shared__ double sy[ORTHO_MAXC];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool staged = k <= BS_MAXK;
+    if (staged)
+        for (int e = tid; e < k * k; e += blockDim.x) {
+            const int c = e / k, i = e - c * k;
+            if (i <= c) sR[c * BS_MAXK + i] = st.R[(size_t)c * ldh + i];
+        }
+    __syncthreads();
+    if (tid >= 32) return;
     for (int i = k - 1; i >= 0; --i) {
-        double s = st.g[i];
-        for (int c = i + 1; c < k; ++c) s -= st.R[(size_t)c * ldh + i] * st.y[c];
-        st.y[i] = s / st.R[(size_t)i * ldh + i];
+        double part = 0.0;
+        for (int c = i + 1 + lane; c < k; c += 32)
+            part = fma(staged ? sR[c * BS_MAXK + i] : st.R[(size_t)c * ldh + i], sy[c], part);
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        if (lane == 0)
+            sy[i] = (st.g[i] - part) / (staged ? sR[i * BS_MAXK + i] : st.R[(size_t)i * ldh + i]);
+        __syncwarp();
     }
+    for (int i = lane; i < k; i += 32) st.y[i] = sy[i];
 }
 
 int32_t launch_backsolve(const GmresState& st, int ldh, int k, cudaStream_t s) {
-    k_backsolve<<<1, 32, 0, s>>>(st, ldh, k);
+    k_backsolve<<<1, 256, 0, s>>>(st, ldh, k);
     ++g_launches;
     return check_launch("k_backsolve");
 }
