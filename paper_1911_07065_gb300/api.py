@@ -274,8 +274,16 @@ def solve_host(rowptr: np.ndarray, colind: np.ndarray, vals: np.ndarray, b: np.n
                v0: np.ndarray, d: int, m: int = 50, tol: float = 1e-10,
                device="cuda", timing: bool = False):
     """End-to-end call from host arrays: copy CSR, b and v0 to the device,
-    build the polynomial, solve, copy x back.  Returns (x, roots, stats)."""
+    build the polynomial, solve, copy x back.  Returns (x, roots, stats).
+
+    The inputs may be NumPy arrays (page-locked here, on every call) or CPU
+    tensors already in pinned memory (copied as they are: the fast path for
+    repeated calls)."""
     def pinned(a, dt):
+        if isinstance(a, torch.Tensor):
+            tdt = torch.int32 if dt == np.int32 else torch.float64
+            t = a if a.dtype == tdt else a.to(tdt)
+            return t if t.is_pinned() else t.contiguous().pin_memory()
         t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
         return t.pin_memory()
     rp = pinned(rowptr, np.int32).to(device, non_blocking=True)

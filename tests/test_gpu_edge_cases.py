@@ -12,6 +12,7 @@
   breaks down (n < d): per-system degrees differ, the shorter step tables are
   padded with no-ops; roots, iteration counts and solutions against the
   oracle.
+* The end-to-end call from host memory with NumPy or pinned inputs.
 """
 import numpy as np
 import pytest
@@ -116,3 +117,23 @@ def test_batched_mixed_degrees_with_breakdown(env):
     degrees = {info["roots"][s].n_orig for s in range(len(probs))}
     assert len(degrees) > 1, degrees
     _check_against_oracle(probs, Xs, info, d, m, tol)
+
+
+def test_solve_host_numpy_and_pinned_inputs(env):
+    """The end-to-end call from host memory: NumPy arrays (page-locked by
+    the call) and tensors already in pinned memory give the same solution,
+    whose true residual meets the tolerance; iterations against the
+    oracle's PP-GMRES with the same roots."""
+    p, torch = env
+    P = synth.problem("cd2d_50")
+    x1, R1, s1 = p.solve_host(P.A.rowptr, P.A.colind, P.A.vals, P.b, P.v0, P.d, P.m, P.tol)
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+              for a in (P.A.rowptr, P.A.colind, P.A.vals, P.b, P.v0)]
+    x2, R2, s2 = p.solve_host(*pinned, P.d, P.m, P.tol)
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(R1.complex(), R2.complex())
+    As = P.A.to_scipy()
+    rel = np.linalg.norm(P.b - As @ x1) / np.linalg.norm(P.b)
+    assert s1["converged"] == 1 and rel <= P.tol
+    _, so = gmres.pp_gmres(As, R1.complex(), P.b, P.m, P.tol)
+    assert abs(s1["iters"] - so.iters) <= 2
