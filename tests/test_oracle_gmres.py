@@ -195,3 +195,29 @@ def test_example5_pp50_cuts_mvps_about_threefold():
     ratio = (spp.mvps + 50) / s0.mvps     # + 50: the construction's GMRES(50)
     assert 0.5 * ratio_paper < ratio < 2.0 * ratio_paper
     assert 0.5 < s0.mvps / nums["ex5_gmres_mvps"] < 2.0
+
+
+def test_estimate_4_1_doubling_the_degree_about_halves_the_mvps():
+    """Estimate 4.1 (Section 4, from the Chebyshev model of a composed
+    polynomial): for a real spectrum in [a, b] with 0 < a << b, PP(d)-GMRES(m)
+    needs about 1/d of the matrix-vector products of GMRES(m), so doubling d
+    about halves them; Example 11 / Table 4.1 (A = diag(i^2/n)) shows ratios
+    a little above one half.  Orthogonalisation (dot products) falls faster
+    than the mvps.  Here n = 2000 (the paper: 20,000), GMRES(50), tol 1e-10,
+    d = 8, 16, 32, 64 (measured ratios about 0.58, 0.57, 0.45)."""
+    n = 2000
+    As = sp.diags(synth.ex11_diagonal(n)).tocsr()
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(n)
+    b /= np.linalg.norm(b)
+    v0 = rng.standard_normal(n)
+    runs = []
+    for d in (8, 16, 32, 64):
+        roots = poly.build_poly(As, d, v0).roots
+        _, st = gmres.pp_gmres(As, roots, b, 50, 1e-10, max_cycles=5000)
+        assert st.converged and st.true_relres <= 1e-10
+        runs.append(st)
+    for lo, hi in zip(runs[:-1], runs[1:]):
+        r_mvps = hi.mvps / lo.mvps
+        assert 0.35 <= r_mvps <= 0.75, r_mvps
+        assert hi.dots / lo.dots < r_mvps
