@@ -153,6 +153,49 @@ __device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T
     }
 }
 
+// Rows per thread: FP32 tiles take two rows per thread (512 rows per CTA),
+// so each CTA's latency-bound phases (row pointers, staging, gathers) serve
+// twice the bytes; FP64 keeps one (its 32 registers allow 8 CTAs per SM).
+template <typename T>
+__host__ __device__ constexpr int step_rpt() { return sizeof(T) == 4 ? 2 : 1; }
+
+// one row's multiply-adds over its staged nonzeros [lo, hi): four gathers in
+// flight, then the last 1-3 (FP32: issued together; FP64: one at a time)
+template <typename T, bool WIDE_TAIL>
+__device__ __forceinline__ T row_dot(const T* sval, const int32_t* scol, const T* __restrict__ x,
+                                     int32_t k, int32_t hi, T acc) {
+    for (; k + 4 <= hi; k += 4) {
+        const T v0 = sval[k], v1 = sval[k + 1], v2 = sval[k + 2], v3 = sval[k + 3];
+        const T x0 = __ldg(x + scol[k]), x1 = __ldg(x + scol[k + 1]);
+        const T x2 = __ldg(x + scol[k + 2]), x3 = __ldg(x + scol[k + 3]);
+        acc = fma(v0, x0, acc);
+        acc = fma(v1, x1, acc);
+        acc = fma(v2, x2, acc);
+        acc = fma(v3, x3, acc);
+    }
+    const int rem = hi - k;
+    if constexpr (!WIDE_TAIL) {
+#pragma unroll 1
+        for (; k < hi; ++k) acc = fma(sval[k], __ldg(x + scol[k]), acc);
+    } else if (rem > 0) {
+        const T v0 = sval[k];
+        const T x0 = __ldg(x + scol[k]);
+        T v1 = T(0), x1 = T(0), v2 = T(0), x2 = T(0);
+        if (rem > 1) {
+            v1 = sval[k + 1];
+            x1 = __ldg(x + scol[k + 1]);
+        }
+        if (rem > 2) {
+            v2 = sval[k + 2];
+            x2 = __ldg(x + scol[k + 2]);
+        }
+        acc = fma(v0, x0, acc);
+        if (rem > 1) acc = fma(v1, x1, acc);
+        if (rem > 2) acc = fma(v2, x2, acc);
+    }
+    return acc;
+}
+
 // PF: prefetch the tile one resident wave ahead into L2 (launched when the
 // matrix is not held in an L2 set-aside)
 template <typename T, int OP, bool PF>
@@ -163,14 +206,17 @@ k_spmv_step(const StepArgs<T> a) {
     // slower in FP32, which keeps per-element copies from the chunk start
     constexpr bool V16 = sizeof(T) == 8;
     constexpr int PAD = V16 ? 4 : 0;
-    __shared__ __align__(16) T sval[SPMV_CHUNK + PAD];
-    __shared__ __align__(16) int32_t scol[SPMV_CHUNK + PAD];
-    __shared__ int32_t srp[SPMV_ROWS + 1];
+    constexpr int RPT = step_rpt<T>();
+    constexpr int ROWS = SPMV_ROWS * RPT;      // rows per CTA
+    constexpr int CHUNK = SPMV_CHUNK * RPT;    // nonzeros staged per chunk
+    __shared__ __align__(16) T sval[CHUNK + PAD];
+    __shared__ __align__(16) int32_t scol[CHUNK + PAD];
+    __shared__ int32_t srp[ROWS + 1];
     __shared__ double sred[SPMV_ROWS / 32];
 
-    const int64_t row0 = (int64_t)blockIdx.x * SPMV_ROWS;
+    const int64_t row0 = (int64_t)blockIdx.x * ROWS;
     const int tid = threadIdx.x;
-    const int nrows = (int)(((int64_t)a.n - row0) < SPMV_ROWS ? ((int64_t)a.n - row0) : SPMV_ROWS);
+    const int nrows = (int)(((int64_t)a.n - row0) < ROWS ? ((int64_t)a.n - row0) : ROWS);
     const uint64_t pol = l2_policy(a.flags & F_KEEP_A);
     // Programmatic dependent launch: the next step in the stream may start
     // now; everything up to griddepcontrol.wait reads only the matrix, which
@@ -180,11 +226,11 @@ k_spmv_step(const StepArgs<T> a) {
     // range is read now, beside this tile's row pointers.  CTAs of the last
     // wave prefetch the matrix tiles of the next step's first wave instead
     // (a chain's next step reads the same matrix).
-    int64_t prow = row0 + (int64_t)a.pf_ahead * SPMV_ROWS;
+    int64_t prow = row0 + (int64_t)a.pf_ahead * ROWS;
     const bool wrap = prow >= a.n;
-    if (wrap) prow -= (int64_t)gridDim.x * SPMV_ROWS;
+    if (wrap) prow -= (int64_t)gridDim.x * ROWS;
     const bool pf = PF && tid == 0 && a.pf_ahead > 0 && prow >= 0 && prow < a.n;
-    const int64_t prow1 = min(prow + SPMV_ROWS, (int64_t)a.n);
+    const int64_t prow1 = min(prow + ROWS, (int64_t)a.n);
     int32_t pk0 = 0, pk1 = 0;
     if (pf) {
         pk0 = __ldg(a.rowptr + prow);
@@ -194,12 +240,18 @@ k_spmv_step(const StepArgs<T> a) {
     __syncthreads();
     const int32_t k0 = srp[0];
     const int32_t k1 = srp[nrows];
-    const int32_t my_lo = (tid < nrows) ? srp[tid] : k1;
-    const int32_t my_hi = (tid < nrows) ? srp[tid + 1] : k1;
+    // thread tid owns rows tid and (RPT = 2) tid + SPMV_ROWS of the tile
+    int32_t my_lo[RPT], my_hi[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SPMV_ROWS;
+        my_lo[q] = (t < nrows) ? srp[t] : k1;
+        my_hi[q] = (t < nrows) ? srp[t + 1] : k1;
+    }
     // element k of the current chunk sits at sval / scol [k - base], base =
     // c0 & ~3 with 16-byte copies, else c0
     {
-        const int32_t c1 = min(k1, k0 + SPMV_CHUNK);
+        const int32_t c1 = min(k1, k0 + CHUNK);
         const int32_t base = V16 ? (k0 & ~3) : k0;
         stage_chunk<T, V16>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS, pol);
     }
@@ -218,68 +270,63 @@ k_spmv_step(const StepArgs<T> a) {
 
     // The epilogue's row-aligned inputs do not depend on the product: load
     // them now, so their latency overlaps the staging and the gathers.
-    const bool live = tid < nrows;
-    const int64_t rr = row0 + tid;
-    T e0 = T(0), e1 = T(0), e2 = T(0);
-    if (live) {
-        if (a.a0) e0 = __ldg(a.a0 + rr);
-        if (a.a1 && !(a.flags & F_PZERO)) e1 = a.a1[rr];
-        if (a.a2 && (a.flags & F_FINAL)) e2 = __ldg(a.a2 + rr);
+    T e0[RPT], e1[RPT], e2[RPT], acc[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        e0[q] = e1[q] = e2[q] = acc[q] = T(0);
+        const int t = tid + q * SPMV_ROWS;
+        if (t < nrows) {
+            const int64_t rr = row0 + t;
+            if (a.a0) e0[q] = __ldg(a.a0 + rr);
+            if (a.a1 && !(a.flags & F_PZERO)) e1[q] = a.a1[rr];
+            if (a.a2 && (a.flags & F_FINAL)) e2[q] = __ldg(a.a2 + rr);
+        }
     }
 
-    T acc = T(0);
-    for (int32_t c0 = k0; c0 < k1; c0 += SPMV_CHUNK) {
-        const int32_t c1 = min(k1, c0 + SPMV_CHUNK);
+    for (int32_t c0 = k0; c0 < k1; c0 += CHUNK) {
+        const int32_t c1 = min(k1, c0 + CHUNK);
         const int32_t base = V16 ? (c0 & ~3) : c0;
         if (c0 != k0) {   // the first chunk was issued before the wait
             stage_chunk<T, V16>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS, pol);
         }
         cp_async_wait_all();
         __syncthreads();
-        const int32_t lo = max(my_lo, c0) - base;
-        const int32_t hi = min(my_hi, c1) - base;
         // exactly one FMA per nonzero (GB300 issues two FP64 operations per
-        // clock per SM), with the gathers of four nonzeros in flight before
-        // their multiply-adds; summation stays in column order
-        int32_t k = lo;
-        for (; k + 4 <= hi; k += 4) {
-            const T v0 = sval[k], v1 = sval[k + 1], v2 = sval[k + 2], v3 = sval[k + 3];
-            const T x0 = __ldg(a.x + scol[k]), x1 = __ldg(a.x + scol[k + 1]);
-            const T x2 = __ldg(a.x + scol[k + 2]), x3 = __ldg(a.x + scol[k + 3]);
-            acc = fma(v0, x0, acc);
-            acc = fma(v1, x1, acc);
-            acc = fma(v2, x2, acc);
-            acc = fma(v3, x3, acc);
-        }
-        // the last 1-3 nonzeros.  FP32: their gathers issued together, the
-        // multiply-adds (only for existing entries) in column order.  FP64
-        // keeps one at a time: the wider form took 40 registers (6 instead of
-        // 8 CTAs per SM) and measured 13 % slower on the 2-D chains.
-        const int rem = hi - k;
-        if constexpr (V16) {
-#pragma unroll 1
-            for (; k < hi; ++k) acc = fma(sval[k], __ldg(a.x + scol[k]), acc);
-        } else if (rem > 0) {
-            const T v0 = sval[k];
-            const T x0 = __ldg(a.x + scol[k]);
-            T v1 = T(0), x1 = T(0), v2 = T(0), x2 = T(0);
-            if (rem > 1) {
-                v1 = sval[k + 1];
-                x1 = __ldg(a.x + scol[k + 1]);
+        // clock per SM); summation stays in column order within each row.
+        // The last 1-3 nonzeros: FP32 issues their gathers together; FP64
+        // takes them one at a time (the wider form took 40 registers, 6
+        // instead of 8 CTAs per SM, and measured 13 % slower on 2-D chains).
+        if constexpr (RPT == 1) {
+            const int32_t lo = max(my_lo[0], c0) - base;
+            const int32_t hi = min(my_hi[0], c1) - base;
+            acc[0] = row_dot<T, !V16>(sval, scol, a.x, lo, hi, acc[0]);
+        } else {
+            // two rows: their four-wide batches in lockstep (eight gathers
+            // in flight), then each row's remainder
+            int32_t ka = max(my_lo[0], c0) - base, kb = max(my_lo[1], c0) - base;
+            const int32_t ha = min(my_hi[0], c1) - base, hb = min(my_hi[1], c1) - base;
+            for (; ka + 4 <= ha && kb + 4 <= hb; ka += 4, kb += 4) {
+                const T va0 = sval[ka], va1 = sval[ka + 1], va2 = sval[ka + 2], va3 = sval[ka + 3];
+                const T vb0 = sval[kb], vb1 = sval[kb + 1], vb2 = sval[kb + 2], vb3 = sval[kb + 3];
+                const T xa0 = __ldg(a.x + scol[ka]), xa1 = __ldg(a.x + scol[ka + 1]);
+                const T xa2 = __ldg(a.x + scol[ka + 2]), xa3 = __ldg(a.x + scol[ka + 3]);
+                const T xb0 = __ldg(a.x + scol[kb]), xb1 = __ldg(a.x + scol[kb + 1]);
+                const T xb2 = __ldg(a.x + scol[kb + 2]), xb3 = __ldg(a.x + scol[kb + 3]);
+                acc[0] = fma(va3, xa3, fma(va2, xa2, fma(va1, xa1, fma(va0, xa0, acc[0]))));
+                acc[1] = fma(vb3, xb3, fma(vb2, xb2, fma(vb1, xb1, fma(vb0, xb0, acc[1]))));
             }
-            if (rem > 2) {
-                v2 = sval[k + 2];
-                x2 = __ldg(a.x + scol[k + 2]);
-            }
-            acc = fma(v0, x0, acc);
-            if (rem > 1) acc = fma(v1, x1, acc);
-            if (rem > 2) acc = fma(v2, x2, acc);
+            acc[0] = row_dot<T, true>(sval, scol, a.x, ka, ha, acc[0]);
+            acc[1] = row_dot<T, true>(sval, scol, a.x, kb, hb, acc[1]);
         }
         __syncthreads();
     }
 
     double sq = 0.0;
-    if (live) step_epilogue<T, OP>(a, rr, acc, e0, e1, e2, sq);
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SPMV_ROWS;
+        if (t < nrows) step_epilogue<T, OP>(a, row0 + t, acc[q], e0[q], e1[q], e2[q], sq);
+    }
     if constexpr (OP == OP_RESID) {
         // deterministic block reduction of ||r||^2
         for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
@@ -422,7 +469,8 @@ static cudaError_t launch_op(cudaLaunchConfig_t& cfg, int op, const StepArgs<T>&
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     if (a_in.n <= 0) return 0;
-    const int grid = spmv_grid_blocks(a_in.n);
+    const int rows = SPMV_ROWS * step_rpt<T>();
+    const int grid = (int)(((int64_t)a_in.n + rows - 1) / rows);
     StepArgs<T> a = a_in;
     // prefetch ahead by one resident wave, unless the matrix is held in an
     // L2 set-aside (measured: the prefetches then cost more than they save)
