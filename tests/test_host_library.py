@@ -147,3 +147,38 @@ def test_csr_validation(ppg):
     rp = A.rowptr.copy()
     rp[5] = rp[6] + 1
     assert ppg.csr_validate_host(rp, A.colind) == -2
+
+
+def test_header_is_plain_c_and_links(ppg, tmp_path):
+    """A C99 program (no C++ anywhere) includes the header, links the
+    library and calls host-only entry points: the ABI needs no C++ or torch
+    on the caller's side."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "ppgmres.h"
+int main(void) {
+    ppg_opts o;
+    double re[3] = {1.0, 4.0, 2.0}, im[3] = {0.0, 0.0, 0.0}, ro[3], io[3];
+    ppg_default_opts(&o);
+    if (ppg_abi_version() != 1 || o.max_cycles <= 0) return 1;
+    if (ppg_leja_order(3, re, im, ro, io) != PPG_OK) return 2;
+    /* the largest modulus first (modified Leja order) */
+    if (ro[0] != 4.0) return 3;
+    printf("%s\n", ppg_strerror(PPG_ERR_ARG));
+    return 0;
+}
+''')
+    libdir = os.path.dirname(ppg.lib._name)
+    exe = tmp_path / "abi"
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+           "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lppgmres",
+           "-Wl,-rpath," + libdir, "-o", str(exe)]
+    subprocess.run(cmd, check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.strip() == ppg.lib.ppg_strerror(-1).decode()
