@@ -13,6 +13,7 @@
   padded with no-ops; roots, iteration counts and solutions against the
   oracle.
 * The end-to-end call from host memory with NumPy or pinned inputs.
+* Degenerate sizes: a matrix without nonzeros and a 1 x 1 matrix.
 """
 import numpy as np
 import pytest
@@ -137,3 +138,33 @@ def test_solve_host_numpy_and_pinned_inputs(env):
     assert s1["converged"] == 1 and rel <= P.tol
     _, so = gmres.pp_gmres(As, R1.complex(), P.b, P.m, P.tol)
     assert abs(s1["iters"] - so.iters) <= 2
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_empty_and_one_by_one_matrices(env, dtype):
+    """Degenerate sizes: a 5 x 5 matrix with no nonzeros (y = A x = 0, and
+    p(A) v reduces to the constant and linear terms the roots leave) and a
+    1 x 1 matrix (p(A) v is the scalar polynomial); against the oracle's
+    Algorithm 3 (float32 for FP32) and y = A x."""
+    p, torch = env
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    R = p.Roots.from_complex(ROOTS)
+    cases = [
+        synth.CSRHost(5, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0)),
+        synth.CSRHost(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0])),
+    ]
+    for A in cases:
+        Ad = dev_csr(p, torch, A, dtype=tdt)
+        v = np.random.default_rng(A.n).standard_normal(A.n)
+        vd = to_dev(torch, v, tdt)
+        As = A.to_scipy()
+        y = p.spmv(Ad, vd).cpu().numpy().astype(np.float64)
+        assert np.allclose(y, As @ v.astype(y.dtype), rtol=1e-6, atol=0)
+        got = p.apply_poly(Ad, R, vd).cpu().numpy().astype(np.float64)
+        if dtype == "f64":
+            ref = poly.apply_p(As, ROOTS, v)
+            assert np.allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+        else:
+            ref = gmres.apply_p32(As.astype(np.float32), gmres._roots32(ROOTS),
+                                  v.astype(np.float32)).astype(np.float64)
+            assert np.allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
