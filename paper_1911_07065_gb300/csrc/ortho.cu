@@ -89,28 +89,52 @@ __device__ __forceinline__ bool last_block_done(unsigned* counter) {
 // per trip, so 2 (NQ + 1) loads are in flight.  NQ is a compile-time width:
 // a predicated-off FP64 FMA still occupies the FP64 pipe on GB300, so the
 // last, narrower chunk of columns must not issue FMAs for missing columns.
-template <int NQ>
+template <int NQ, bool VEC2>
 __device__ __forceinline__ void dot_rows(const double* const* col, const double* __restrict__ w,
                                          int64_t r, int64_t stride, int64_t n, double* acc) {
-    for (; r + stride < n; r += 2 * stride) {
-        const double w0 = w[r], w1 = w[r + stride];
+    if constexpr (VEC2) {
+        // rows 2p and 2p+1 with one 16-byte load per column (half the load
+        // instructions of two 8-byte loads); an odd last row goes to the one
+        // thread whose pair index stops at n / 2
+        const int64_t np = n >> 1;
+        int64_t p = r;
+        for (; p < np; p += stride) {
+            const double2 w2 = __ldg(reinterpret_cast<const double2*>(w) + p);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const double a0 = __ldcs(col[q] + r), a1 = __ldcs(col[q] + r + stride);
-            acc[q] = fma(a1, w1, fma(a0, w0, acc[q]));
+            for (int q = 0; q < NQ; ++q) {
+                const double2 a = __ldcs(reinterpret_cast<const double2*>(col[q]) + p);
+                acc[q] = fma(a.y, w2.y, fma(a.x, w2.x, acc[q]));
+            }
         }
-    }
-    if (r < n) {
-        const double w0 = w[r];
+        if ((n & 1) && p == np) {
+            const double w0 = w[n - 1];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + r), w0, acc[q]);
+            for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + n - 1), w0, acc[q]);
+        }
+    } else {
+        // acc[q] += sum over this thread's rows of col[q][r] w[r], two rows
+        // per trip, so 2 (NQ + 1) loads are in flight
+        for (; r + stride < n; r += 2 * stride) {
+            const double w0 = w[r], w1 = w[r + stride];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double a0 = __ldcs(col[q] + r), a1 = __ldcs(col[q] + r + stride);
+                acc[q] = fma(a1, w1, fma(a0, w0, acc[q]));
+            }
+        }
+        if (r < n) {
+            const double w0 = w[r];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] = fma(__ldcs(col[q] + r), w0, acc[q]);
+        }
     }
 }
 
 // hout[c] = sum_r V[c][r] w[r] for c < ncol, and hout[ncol] = w.w when
 // with_self.  Grid: x = row blocks (grid-stride), y = chunks of eight
 // columns, so every column chunk streams in parallel.
-__global__ void __launch_bounds__(ORTHO_THREADS)
+template <bool VEC2>
+__global__ void __launch_bounds__(ORTHO_THREADS, 4)
 k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __restrict__ w,
        int32_t n, int with_self, double* part, unsigned* counter, double* hout) {
     __shared__ double sred[ORTHO_WARPS][DOT_CH];
@@ -134,14 +158,14 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
     const int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
     switch (nq) {
-        case 8: dot_rows<8>(col, w, r, stride, n, acc); break;
-        case 7: dot_rows<7>(col, w, r, stride, n, acc); break;
-        case 6: dot_rows<6>(col, w, r, stride, n, acc); break;
-        case 5: dot_rows<5>(col, w, r, stride, n, acc); break;
-        case 4: dot_rows<4>(col, w, r, stride, n, acc); break;
-        case 3: dot_rows<3>(col, w, r, stride, n, acc); break;
-        case 2: dot_rows<2>(col, w, r, stride, n, acc); break;
-        default: dot_rows<1>(col, w, r, stride, n, acc); break;
+        case 8: dot_rows<8, VEC2>(col, w, r, stride, n, acc); break;
+        case 7: dot_rows<7, VEC2>(col, w, r, stride, n, acc); break;
+        case 6: dot_rows<6, VEC2>(col, w, r, stride, n, acc); break;
+        case 5: dot_rows<5, VEC2>(col, w, r, stride, n, acc); break;
+        case 4: dot_rows<4, VEC2>(col, w, r, stride, n, acc); break;
+        case 3: dot_rows<3, VEC2>(col, w, r, stride, n, acc); break;
+        case 2: dot_rows<2, VEC2>(col, w, r, stride, n, acc); break;
+        default: dot_rows<1, VEC2>(col, w, r, stride, n, acc); break;
     }
     warp_reduce8(acc, lane);
     if ((lane & 3) == 0) sred[warp][lane >> 2] = acc[0];
@@ -166,7 +190,8 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
 }
 
 // w[r] -= sum_c V[c][r] h[c]; with_norm: nout[0] = ||w||^2 afterwards
-__global__ void __launch_bounds__(ORTHO_THREADS)
+template <bool VEC2>
+__global__ void __launch_bounds__(ORTHO_THREADS, 5)
 k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
            const double* __restrict__ h, int with_norm, double* part, unsigned* counter,
            double* nout) {
@@ -180,19 +205,44 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     double nacc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
     int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
-    // two rows per trip: two independent FMA chains, 2 loads per column in
-    // flight, exactly one FMA per element of V
-    for (; r + stride < n; r += 2 * stride) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int c = 0; c < ncol; ++c) {
-            const double hc = sh[c];
-            s0 = fma(__ldcs(V + c * ldv + r), hc, s0);
-            s1 = fma(__ldcs(V + c * ldv + r + stride), hc, s1);
+    if constexpr (VEC2) {
+        // rows 2p and 2p+1: one 16-byte load per column, two FMA chains,
+        // exactly one FMA per element of V; an odd last row goes to the one
+        // thread whose pair index stops at n / 2
+        const int64_t np = (int64_t)n >> 1;
+        int64_t p = r;
+        for (; p < np; p += stride) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int c = 0; c < ncol; ++c) {
+                const double hc = sh[c];
+                const double2 v = __ldcs(reinterpret_cast<const double2*>(V + c * ldv) + p);
+                s0 = fma(v.x, hc, s0);
+                s1 = fma(v.y, hc, s1);
+            }
+            double2 w2 = reinterpret_cast<double2*>(w)[p];
+            w2.x -= s0;
+            w2.y -= s1;
+            reinterpret_cast<double2*>(w)[p] = w2;
+            nacc = fma(w2.y, w2.y, fma(w2.x, w2.x, nacc));
         }
-        const double w0 = w[r] - s0, w1 = w[r + stride] - s1;
-        w[r] = w0;
-        w[r + stride] = w1;
-        nacc = fma(w1, w1, fma(w0, w0, nacc));
+        // the odd last row: taken below by the one thread whose pair index
+        // stopped at n / 2
+        r = ((n & 1) && p == np) ? (int64_t)n - 1 : (int64_t)n;
+    } else {
+        // two rows per trip: two independent FMA chains, 2 loads per column
+        // in flight, exactly one FMA per element of V
+        for (; r + stride < n; r += 2 * stride) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int c = 0; c < ncol; ++c) {
+                const double hc = sh[c];
+                s0 = fma(__ldcs(V + c * ldv + r), hc, s0);
+                s1 = fma(__ldcs(V + c * ldv + r + stride), hc, s1);
+            }
+            const double w0 = w[r] - s0, w1 = w[r + stride] - s1;
+            w[r] = w0;
+            w[r + stride] = w1;
+            nacc = fma(w1, w1, fma(w0, w0, nacc));
+        }
     }
     if (r < n) {
         double s0 = 0.0;
@@ -221,7 +271,7 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
 // SMs), cached per device and kernel slot
 template <typename K>
 static int resident_ctas(K kernel, int slot) {
-    static std::atomic<int> cached[16][2];
+    static std::atomic<int> cached[16][4];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
     int v = cached[dev][slot].load(std::memory_order_relaxed);
@@ -238,7 +288,10 @@ static int resident_ctas(K kernel, int slot) {
     }
     return v;
 }
-static int mdot_slots() { return resident_ctas(k_mdot, 0); }
+// 16-byte (double2) loads when V, its column stride and w allow them
+static bool vec2_ok(const double* V, int64_t ldv, const double* w) {
+    return (((uintptr_t)V | (uintptr_t)w) & 15) == 0 && (ldv & 1) == 0;
+}
 
 int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, int32_t n,
                        bool with_self, double* h_out, const OrthoWs& ws, cudaStream_t s) {
@@ -247,13 +300,17 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, 
     const int nch = (nvals + DOT_CH - 1) / DOT_CH;
     // row blocks x column chunks = one full wave of resident CTAs (at least
     // two rows per thread; the partial-sum buffer holds 1216 row blocks)
-    const int gx = max(1, min(min(mdot_slots() / nch, (n + 2 * ORTHO_THREADS - 1) /
-                                                          (2 * ORTHO_THREADS)),
+    const bool v2 = vec2_ok(V, ldv, w);
+    const int slots = v2 ? resident_ctas(k_mdot<true>, 0) : resident_ctas(k_mdot<false>, 1);
+    const int gx = max(1, min(min(slots / nch, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
                               152 * 8));
     (void)ws.grid;
     const dim3 grid(gx, nch);
-    const cudaError_t e = launch_pdl(k_mdot, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
-                                     with_self ? 1 : 0, ws.part, ws.counter, h_out);
+    const cudaError_t e =
+        v2 ? launch_pdl(k_mdot<true>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
+                        with_self ? 1 : 0, ws.part, ws.counter, h_out)
+           : launch_pdl(k_mdot<false>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
+                        with_self ? 1 : 0, ws.part, ws.counter, h_out);
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_mdot"); return PPG_ERR_CUDA; }
     return check_launch("k_mdot");
@@ -265,12 +322,15 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
     // one wave of resident CTAs, at least two rows per thread, at most the
     // 1216 row blocks the partial-sum buffer holds
-    const int grid = max(1, min(min(resident_ctas(k_gemv_sub, 1),
-                                    (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
+    const bool v2 = vec2_ok(V, ldv, w);
+    const int slots = v2 ? resident_ctas(k_gemv_sub<true>, 2) : resident_ctas(k_gemv_sub<false>, 3);
+    const int grid = max(1, min(min(slots, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
                                 152 * 8));
-    const cudaError_t e = launch_pdl(k_gemv_sub, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv,
-                                     ncol, w, n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1,
-                                     nrm_out);
+    const cudaError_t e =
+        v2 ? launch_pdl(k_gemv_sub<true>, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w,
+                        n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1, nrm_out)
+           : launch_pdl(k_gemv_sub<false>, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv, ncol,
+                        w, n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1, nrm_out);
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_gemv_sub"); return PPG_ERR_CUDA; }
     return check_launch("k_gemv_sub");
