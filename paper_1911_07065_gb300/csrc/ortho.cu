@@ -304,7 +304,7 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, 
     const int slots = v2 ? resident_ctas(k_mdot<true>, 0) : resident_ctas(k_mdot<false>, 1);
     const int gx = max(1, min(min(slots / nch, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
                               152 * 8));
-    (void)ws.grid;
+    // (ws.part holds max(ws.grid, 1216) row blocks of partial sums: gx <= 1216 fits)
     const dim3 grid(gx, nch);
     const cudaError_t e =
         v2 ? launch_pdl(k_mdot<true>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
