@@ -193,7 +193,13 @@ int32_t ppg_apply_poly(const ppg_csr* A, const ppg_roots* r, const void* v,
  * n > PPG_NOALLOC_MAX_N is rejected with PPG_ERR_TOO_LARGE before any work
  * is enqueued.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  All calls share the one array and
+ * first call before any stream capture (a first call made while `stream`
+ * is capturing returns PPG_ERR_ARG and enqueues nothing).  Unlike
+ * ppg_apply_poly it never reserves an L2 set-aside for the matrix, so
+ * apart from that lookup it changes no state of the CUDA context.  The
+ * argument checks are those of ppg_apply_poly (PPG_ERR_ARG for a NULL or
+ * aliased vector, a bad CSR descriptor, or a root list that is not finite,
+ * has a zero root or an unpaired complex root).  All calls share the one array and
  * it keeps the last call's contents (nothing in it needs to start at zero:
  * each call writes every slot before reading it), so calls whose GPU work
  * overlaps -- on different streams or host threads -- race and give wrong

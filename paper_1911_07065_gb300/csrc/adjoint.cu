@@ -89,8 +89,8 @@ int32_t launch_transpose(const ppg_csr* A, int32_t* rowptr_t, int32_t* colind_t,
     int32_t* cursor = work + n;     // [n]
     PPG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)n, s));
     PPG_CUDA(cudaMemsetAsync(rowptr_t, 0, sizeof(int32_t), s));
-    const int gz = max(1, min((nnz + 255) / 256, 152 * 8));
-    const int gn = max(1, min((n + 255) / 256, 152 * 8));
+    const int gz = max(1, min((nnz + 255) / 256, grid_cap(8)));
+    const int gn = max(1, min((n + 255) / 256, grid_cap(8)));
     if (nnz > 0) {
         k_count_cols<<<gz, 256, 0, s>>>(A->colind, nnz, cnt);
         ++g_launches;
@@ -131,7 +131,7 @@ __global__ void k_adjoint_grad(const int32_t* __restrict__ rowptr,
 
 int32_t launch_adjoint_grad(const ppg_csr* A, const double* lam, const double* x,
                             double* gvals, cudaStream_t s) {
-    const int gn = max(1, min((A->n + 255) / 256, 152 * 8));
+    const int gn = max(1, min((A->n + 255) / 256, grid_cap(8)));
     k_adjoint_grad<<<gn, 256, 0, s>>>(A->rowptr, A->colind, lam, x, A->n, gvals);
     ++g_launches;
     return check_launch("k_adjoint_grad");

@@ -3,6 +3,7 @@
 // (Algorithm 4 step 1) and restarted (F)GMRES around the chains (Algorithm 4
 // step 2, plus the FP32-inner flexible form), the stability check of
 // Section 3.5 and the adjoint helpers.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -119,23 +120,25 @@ static T* mbuf(const Buffers& b, int id) {
 template <typename T>
 static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const int32_t* rowptr,
                          const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
-                         const Buffers& bufs, cudaStream_t s, double* bytes_out);
+                         const Buffers& bufs, cudaStream_t s, double* bytes_out,
+                         bool reserve_l2 = true);
 
 template <typename T>
 int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr, const int32_t* colind,
                  const T* vals, int32_t n, int64_t nnz, const Buffers& bufs, cudaStream_t s,
-                 double* bytes_out) {
+                 double* bytes_out, bool reserve_l2) {
     return run_steps<T>(plan, 0, (int)plan.size(), rowptr, colind, vals, n, nnz, bufs, s,
-                        bytes_out);
+                        bytes_out, reserve_l2);
 }
 
 // steps [i0, i1) of a plan, in order
 template <typename T>
 static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const int32_t* rowptr,
                          const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
-                         const Buffers& bufs, cudaStream_t s, double* bytes_out) {
+                         const Buffers& bufs, cudaStream_t s, double* bytes_out,
+                         bool reserve_l2) {
     double bytes = 0.0;
-    const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3);
+    const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3, reserve_l2);
     for (int i = i0; i < i1; ++i) {
         const Step& st = plan[(size_t)i];
         if (st.op == OP_AXPY) {
@@ -171,10 +174,10 @@ static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const in
 
 template int32_t run_plan<double>(const std::vector<Step>&, const int32_t*, const int32_t*,
                                   const double*, int32_t, int64_t, const Buffers&, cudaStream_t,
-                                  double*);
+                                  double*, bool);
 template int32_t run_plan<float>(const std::vector<Step>&, const int32_t*, const int32_t*,
                                  const float*, int32_t, int64_t, const Buffers&, cudaStream_t,
-                                 double*);
+                                 double*, bool);
 
 // ---------------------------------------------------------------------------
 // Workspace: one stream-ordered allocation carved into aligned pieces
@@ -193,6 +196,25 @@ int32_t setup_device_pool() {
     return PPG_OK;
 }
 
+int device_sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    int v = dev >= 0 ? cached[dev].load(std::memory_order_relaxed) : 0;
+    if (v == 0) {
+        if (dev < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                           cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        if (dev >= 0) cached[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 static int64_t pad_ld(int32_t n) { return ((int64_t)n + 63) / 64 * 64; }
 
 // Pinned host buffer for the per-step status read (one per host thread,
@@ -208,7 +230,7 @@ static int32_t status_buffer(double** out) {
     return PPG_OK;
 }
 
-static int32_t check_csr(const ppg_csr* A, int dtype_required) {
+int32_t check_csr(const ppg_csr* A, int dtype_required) {
     if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && (!A->colind || !A->vals)))
         return PPG_ERR_ARG;
     if (A->dtype != PPG_F64 && A->dtype != PPG_F32) return PPG_ERR_ARG;
@@ -216,7 +238,7 @@ static int32_t check_csr(const ppg_csr* A, int dtype_required) {
     return PPG_OK;
 }
 
-static int32_t check_roots(const ppg_roots* r) {
+int32_t check_roots(const ppg_roots* r) {
     if (!r || r->n_total < 1 || !r->re || !r->im) return PPG_ERR_ARG;
     const int d = r->n_total;
     for (int i = 0; i < d;) {

@@ -566,7 +566,7 @@ __global__ void k_cast32(const float* x, double* y, int64_t n) {
 
 int elem_grid(int64_t total) {
     const int64_t g = (total + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, grid_cap(8)));
 }
 
 #define BCHECK(where)                                 \

@@ -12,7 +12,9 @@
 // Host code must not pass the array's name to a kernel (on the host it is
 // only a stand-in for the device symbol); its device address is looked up
 // once per device with cudaGetSymbolAddress, with that device current, on
-// the first call made on that device.
+// the first call made on that device.  Apart from that lookup the entry point
+// changes no state of the context: unlike ppg_apply_poly it never reserves an
+// L2 set-aside for the matrix.
 #include <mutex>
 
 #include "ppg_common.cuh"
@@ -31,13 +33,18 @@ std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // device address of g_noalloc_scratch on the current device (set up on the
-// first call made on that device)
-int32_t scratch_address(void** out) {
+// first call made on that device).  That first call must not be made while
+// `s` is being captured into a graph: the lookup may load the library's
+// device code, which a capture does not allow, so it is refused instead.
+int32_t scratch_address(cudaStream_t s, void** out) {
     int dev = 0;
     PPG_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return PPG_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (g_scratch_addr[dev] == nullptr) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PPG_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return PPG_ERR_ARG;
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -50,21 +57,6 @@ int32_t scratch_address(void** out) {
     return PPG_OK;
 }
 
-bool roots_ok(const ppg_roots* r) {
-    if (!r || r->n_total < 1 || !r->re || !r->im) return false;
-    for (int i = 0; i < r->n_total;) {
-        if (r->im[i] == 0.0) {
-            if (r->re[i] == 0.0) return false;
-            i += 1;
-        } else {
-            if (i + 1 >= r->n_total || r->re[i + 1] != r->re[i] || r->im[i + 1] != -r->im[i])
-                return false;
-            i += 2;
-        }
-    }
-    return true;
-}
-
 }  // namespace
 
 }  // namespace ppg
@@ -73,13 +65,14 @@ using namespace ppg;
 
 extern "C" int32_t ppg_apply_poly_noalloc(const ppg_csr* A, const ppg_roots* r, const void* v,
                                           void* y, void* stream) {
-    if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || (A->nnz > 0 && (!A->colind || !A->vals)))
-        return PPG_ERR_ARG;
-    if (A->dtype != PPG_F64 && A->dtype != PPG_F32) return PPG_ERR_ARG;
-    if (!roots_ok(r) || !v || !y || v == y) return PPG_ERR_ARG;
+    // the same argument checks as ppg_apply_poly
+    PPG_TRY(check_csr(A, -1));
+    PPG_TRY(check_roots(r));
+    if (!v || !y || v == y) return PPG_ERR_ARG;
     if (A->n > PPG_NOALLOC_MAX_N) return PPG_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
     void* base = nullptr;
-    PPG_TRY(scratch_address(&base));
+    PPG_TRY(scratch_address(s, &base));
     // Nothing in the array has to start at zero: within one call every slot
     // is written before it is read (the accumulator is the caller's y).
     const size_t slot = (size_t)PPG_NOALLOC_MAX_N * sizeof(double);
@@ -91,10 +84,11 @@ extern "C" int32_t ppg_apply_poly_noalloc(const ppg_csr* A, const ppg_roots* r, 
     bufs.ptr[B_B] = (char*)base + slot;
     bufs.ptr[B_C] = (char*)base + 2 * slot;
     const std::vector<Step> plan = plan_p(r->re, r->im, r->n_total, false);
-    cudaStream_t s = (cudaStream_t)stream;
+    // reserve_l2 = false: this entry point leaves the context's L2
+    // set-aside as it finds it (the cache hint changes no result)
     if (A->dtype == PPG_F64)
         return run_plan<double>(plan, A->rowptr, A->colind, (const double*)A->vals, A->n,
-                                A->nnz, bufs, s, nullptr);
+                                A->nnz, bufs, s, nullptr, false);
     return run_plan<float>(plan, A->rowptr, A->colind, (const float*)A->vals, A->n, A->nnz,
-                           bufs, s, nullptr);
+                           bufs, s, nullptr, false);
 }

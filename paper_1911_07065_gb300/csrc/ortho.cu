@@ -27,10 +27,12 @@ constexpr int PART_STRIDE = ORTHO_MAXC + 2;
 
 int ortho_grid(int32_t n) {
     const int per = ORTHO_THREADS * 8;   // at least ~8 rows per thread
-    return max(1, min((n + per - 1) / per, 152 * 2));
+    return max(1, min((n + per - 1) / per, grid_cap(2)));
 }
 
-size_t ortho_part_doubles(int grid) { return (size_t)max(grid, 152 * 8) * PART_STRIDE; }
+// partial sums of the CGS2 passes: their grids have at most grid_cap(8) row
+// blocks (the norm kernels at most `grid`)
+size_t ortho_part_doubles(int grid) { return (size_t)max(grid, grid_cap(8)) * PART_STRIDE; }
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -280,9 +282,7 @@ static int resident_ctas(K kernel, int slot) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, ORTHO_THREADS, 0) !=
                 cudaSuccess || occ < 1)
             occ = 4;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms < 1)
-            sms = 152;
+        sms = device_sm_count();
         v = occ * sms;
         cached[dev][slot].store(v, std::memory_order_relaxed);
     }
@@ -299,12 +299,12 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, 
     const int nvals = ncol + (with_self ? 1 : 0);
     const int nch = (nvals + DOT_CH - 1) / DOT_CH;
     // row blocks x column chunks = one full wave of resident CTAs (at least
-    // two rows per thread; the partial-sum buffer holds 1216 row blocks)
+    // two rows per thread; the partial-sum buffer holds grid_cap(8) row blocks)
     const bool v2 = vec2_ok(V, ldv, w);
     const int slots = v2 ? resident_ctas(k_mdot<true>, 0) : resident_ctas(k_mdot<false>, 1);
     const int gx = max(1, min(min(slots / nch, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
-                              152 * 8));
-    // (ws.part holds max(ws.grid, 1216) row blocks of partial sums: gx <= 1216 fits)
+                              grid_cap(8)));
+    // (ws.part holds max(ws.grid, grid_cap(8)) row blocks of partial sums)
     const dim3 grid(gx, nch);
     const cudaError_t e =
         v2 ? launch_pdl(k_mdot<true>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
@@ -321,11 +321,11 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
                           const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
     // one wave of resident CTAs, at least two rows per thread, at most the
-    // 1216 row blocks the partial-sum buffer holds
+    // grid_cap(8) row blocks the partial-sum buffer holds
     const bool v2 = vec2_ok(V, ldv, w);
     const int slots = v2 ? resident_ctas(k_gemv_sub<true>, 2) : resident_ctas(k_gemv_sub<false>, 3);
     const int grid = max(1, min(min(slots, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
-                                152 * 8));
+                                grid_cap(8)));
     const cudaError_t e =
         v2 ? launch_pdl(k_gemv_sub<true>, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w,
                         n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1, nrm_out)
@@ -469,7 +469,7 @@ template <typename TV>
 int32_t launch_gemv_acc(const TV* V, int64_t ldv, int k, const double* y, double* out,
                         int32_t n, bool accumulate, cudaStream_t s) {
     if (k < 0 || k > ORTHO_MAXC) return PPG_ERR_ARG;
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     k_gemv_acc<TV><<<grid, 256, 0, s>>>(V, ldv, k, y, out, n, accumulate ? 1 : 0);
     ++g_launches;
     return check_launch("k_gemv_acc");
@@ -491,7 +491,7 @@ __global__ void k_scale(const double* x, double* y, int32_t n, const double* sp)
 
 int32_t launch_scale(const double* x, double* y, int32_t n, const double* sp,
                      cudaStream_t s) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     const cudaError_t e = launch_pdl(k_scale, dim3(grid), dim3(256), 0, s, x, y, n, sp);
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_scale"); return PPG_ERR_CUDA; }
@@ -520,7 +520,7 @@ __global__ void k_norm2_part(const double* a, const double* b, int32_t n, double
 
 int32_t launch_norm2_part(const double* x, int32_t n, double* part, cudaStream_t s,
                           int* nparts) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 4));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(4)));
     k_norm2_part<false><<<grid, 256, 0, s>>>(x, nullptr, n, part);
     ++g_launches;
     *nparts = grid;
@@ -529,7 +529,7 @@ int32_t launch_norm2_part(const double* x, int32_t n, double* part, cudaStream_t
 
 int32_t launch_diff_norm2_part(const double* a, const double* b, int32_t n, double* part,
                                cudaStream_t s, int* nparts) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 4));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(4)));
     k_norm2_part<true><<<grid, 256, 0, s>>>(a, b, n, part);
     ++g_launches;
     *nparts = grid;
@@ -573,13 +573,13 @@ __global__ void k_cast_f32_f64(const float* x, double* y, int32_t n) {
 }
 
 int32_t launch_cast_f64_f32(const double* x, float* y, int32_t n, cudaStream_t s) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     k_cast_f64_f32<<<grid, 256, 0, s>>>(x, y, n);
     ++g_launches;
     return check_launch("k_cast_f64_f32");
 }
 int32_t launch_cast_f32_f64(const float* x, double* y, int32_t n, cudaStream_t s) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     k_cast_f32_f64<<<grid, 256, 0, s>>>(x, y, n);
     ++g_launches;
     return check_launch("k_cast_f32_f64");
@@ -591,7 +591,7 @@ __global__ void k_fill(double* x, double v, int32_t n) {
         x[r] = v;
 }
 int32_t launch_fill(double* x, double v, int32_t n, cudaStream_t s) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     k_fill<<<grid, 256, 0, s>>>(x, v, n);
     ++g_launches;
     return check_launch("k_fill");
@@ -606,7 +606,7 @@ __global__ void k_axpby(T a, const T* x, T b, const T* y, T* out, int32_t n) {
 }
 template <typename T>
 int32_t launch_axpby(T a, const T* x, T b, const T* y, T* out, int32_t n, cudaStream_t s) {
-    const int grid = max(1, min((n + 255) / 256, 152 * 8));
+    const int grid = max(1, min((n + 255) / 256, grid_cap(8)));
     k_axpby<T><<<grid, 256, 0, s>>>(a, x, b, y, out, n);
     ++g_launches;
     return check_launch("k_axpby");

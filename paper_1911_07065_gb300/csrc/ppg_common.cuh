@@ -35,6 +35,12 @@ extern thread_local int64_t g_launches;   // kernels launched by this thread
 
 int32_t check_launch(const char* where);
 
+// Argument checks shared by the entry points: a CSR descriptor (dtype
+// PPG_F64 or PPG_F32; dtype_required < 0 accepts either) and a root list
+// (finite values, no zero root, conjugate pairs adjacent and exact).
+int32_t check_csr(const ppg_csr* A, int dtype_required);
+int32_t check_roots(const ppg_roots* r);
+
 // Programmatic dependent launch.  A kernel launched with launch_pdl may
 // start while the previous kernel in the stream finishes; it must call
 // PPG_PDL_WAIT() before touching any global data that earlier work writes
@@ -96,6 +102,11 @@ struct Arena {
 // Keep freed scratch cached in the device's default pool (once per device).
 int32_t setup_device_pool();
 
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sm_count();
+// Grid cap for grid-stride elementwise kernels: `per_sm` CTAs per SM.
+inline int grid_cap(int per_sm) { return per_sm * device_sm_count(); }
+
 // ---------------------------------------------------------------------------
 // Fused SpMV-root step (one pass over A per root; Algorithms 1 and 3)
 // ---------------------------------------------------------------------------
@@ -146,8 +157,12 @@ int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s);
 template <typename T>
 int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_t s);
 
-// F_KEEP_A when the matrix plus `nvec` work vectors fit comfortably in L2
-int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec);
+// F_KEEP_A when the matrix plus `nvec` work vectors fit comfortably in L2.
+// The first such request reserves an L2 set-aside for the matrix (a limit of
+// the process's context on the current device); with may_reserve = false
+// nothing is reserved and F_KEEP_A is returned only if a set-aside large
+// enough already exists on this device.
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve = true);
 
 int32_t spmv_grid_blocks(int32_t n);
 
@@ -176,10 +191,12 @@ struct Buffers {
     void* ptr[6];
 };
 
+// reserve_l2 = false: never change the context's L2 set-aside (see keep_a_flag)
 template <typename T>
 int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr,
                  const int32_t* colind, const T* vals, int32_t n, int64_t nnz,
-                 const Buffers& bufs, cudaStream_t s, double* bytes_out);
+                 const Buffers& bufs, cudaStream_t s, double* bytes_out,
+                 bool reserve_l2 = true);
 
 // ---------------------------------------------------------------------------
 // Orthogonalisation and small dense kernels

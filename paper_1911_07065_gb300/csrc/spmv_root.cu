@@ -392,40 +392,66 @@ template int32_t launch_ew_step<double>(int, const StepArgs<double>&, const doub
 
 int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
 
-// Reserve L2 for evict-last (persisting) lines, once per process: without a
-// set-aside the evict-last hint is treated as normal.  This is a limit of
-// this process's context on its current device; it ends with the process.
-static void reserve_l2_for(size_t bytes) {
-    static size_t reserved = 0;
-    if (bytes <= reserved) return;
-    int dev = 0, maxp = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
-        maxp <= 0) {
+// Reserve L2 for evict-last (persisting) lines on the current device: without
+// a set-aside the evict-last hint is treated as normal.  This is a limit of
+// this process's context on that device; it ends with the process.  Returns
+// the set-aside now in place.
+constexpr int kL2Devices = 64;
+static std::atomic<size_t> g_l2_reserved[kL2Devices];
+static std::atomic<int> g_l2_bytes[kL2Devices];
+
+static int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kL2Devices) {
         cudaGetLastError();
-        return;
+        return -1;
     }
-    const size_t want = bytes < (size_t)maxp ? bytes : (size_t)maxp;
-    if (want > reserved && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess)
-        reserved = want;
-    cudaGetLastError();
+    return dev;
 }
 
-int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec) {
-    static int l2_bytes = -1;   // L2 size of the device first used (one GPU per process)
-    if (l2_bytes < 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
-            v = 0;
+static size_t reserve_l2_for(int dev, size_t bytes) {
+    const size_t have = g_l2_reserved[dev].load(std::memory_order_relaxed);
+    if (bytes <= have) return have;
+    int maxp = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        maxp <= 0) {
         cudaGetLastError();
-        l2_bytes = v;
+        return have;
     }
+    const size_t want = bytes < (size_t)maxp ? bytes : (size_t)maxp;
+    if (want > have && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) {
+        g_l2_reserved[dev].store(want, std::memory_order_relaxed);
+        cudaGetLastError();
+        return want;
+    }
+    cudaGetLastError();
+    return have;
+}
+
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve) {
+    const int dev = current_device();
+    if (dev < 0) return 0;
+    int l2 = g_l2_bytes[dev].load(std::memory_order_relaxed);
+    if (l2 == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = -1;
+        }
+        g_l2_bytes[dev].store(v, std::memory_order_relaxed);
+        l2 = v;
+    }
+    if (l2 <= 0) return 0;
     const double a_bytes = (double)nnz * (elem + 4) + 4.0 * (n + 1);
     const double bytes = a_bytes + (double)nvec * n * elem;
-    if (!(bytes <= 0.8 * (double)l2_bytes)) return 0;
-    reserve_l2_for((size_t)(a_bytes * 1.05));
-    return F_KEEP_A;
+    if (!(bytes <= 0.8 * (double)l2)) return 0;
+    const size_t need = (size_t)(a_bytes * 1.05);
+    if (may_reserve) {
+        reserve_l2_for(dev, need);
+        return F_KEEP_A;
+    }
+    // no change to the context: the hint only where a set-aside exists
+    return g_l2_reserved[dev].load(std::memory_order_relaxed) >= need ? F_KEEP_A : 0;
 }
 
 // CTAs of the root-step kernel resident at once (occupancy x SMs), per

@@ -71,3 +71,80 @@ def test_noalloc_float32_and_size_limit():
     assert _call_noalloc(p, torch, Bd, R, vb, yb) == -9     # PPG_ERR_TOO_LARGE
     torch.cuda.synchronize()
     assert torch.all(yb == 0)
+
+
+def test_noalloc_rejects_nonfinite_roots_like_apply_poly():
+    p, torch = ppg_or_skip()
+    A = synth.cd2d(20, 0.5)
+    Ad = dev_csr(p, torch, A)
+    v = to_dev(torch, np.random.default_rng(23).standard_normal(A.n))
+    for bad in (np.inf, -np.inf, np.nan):
+        R = p.Roots.from_complex(np.array([3.0, bad, 2.0], dtype=complex))
+        R.im[1] = 0.0                        # a "real" root of +-inf or NaN
+        y = torch.zeros_like(v)
+        assert _call_noalloc(p, torch, Ad, R, v, y) == -1          # PPG_ERR_ARG
+        y2 = torch.zeros_like(v)
+        rc = p.lib.ppg_apply_poly(Ad.ref(), R.ref(), C.c_void_p(v.data_ptr()),
+                                  C.c_void_p(y2.data_ptr()),
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == -1
+        torch.cuda.synchronize()
+        assert torch.all(y == 0) and torch.all(y2 == 0)
+
+
+class _DefaultPool:
+    """The device's default stream-ordered memory pool, read through the
+    driver API: the pool the library's other entry points allocate from."""
+    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8      # CUmemPool_attribute
+
+    def __init__(self, torch):
+        self.cu = C.CDLL("libcuda.so.1")
+        dev = C.c_int(0)
+        assert self.cu.cuDeviceGet(C.byref(dev), torch.cuda.current_device()) == 0
+        self.pool = C.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(C.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = C.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, C.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = C.c_uint64(0)     # resets the high-water mark to the current use
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, C.byref(zero)) == 0
+
+
+def test_noalloc_allocates_nothing():
+    """The defining contract: around a synchronised call, the default pool's
+    high-water mark of used memory does not rise and the device's free memory
+    does not drop.  The allocating entry point, run the same way, does raise
+    the mark, which shows that the probe sees stream-ordered allocations."""
+    p, torch = ppg_or_skip()
+    A = synth.cd2d(300, 0.7)
+    Ad = dev_csr(p, torch, A)
+    R = p.Roots.from_complex(np.array([4.0, 3 + 1j, 3 - 1j, 2.5, 1.7]))
+    v = to_dev(torch, np.random.default_rng(24).standard_normal(A.n))
+    y = torch.empty_like(v)
+    stream = torch.cuda.current_stream()
+    assert _call_noalloc(p, torch, Ad, R, v, y) == 0          # address set up
+    torch.cuda.synchronize()
+    pool = _DefaultPool(torch)
+
+    pool.reset_high()
+    used0 = pool.get(pool.USED_MEM_CURRENT)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        assert _call_noalloc(p, torch, Ad, R, v, y) == 0
+        stream.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) == used0
+    assert torch.cuda.mem_get_info()[0] == free0
+
+    # positive control: ppg_apply_poly takes its work vectors from the pool
+    pool.reset_high()
+    y2 = torch.empty_like(v)
+    rc = p.lib.ppg_apply_poly(Ad.ref(), R.ref(), C.c_void_p(v.data_ptr()),
+                              C.c_void_p(y2.data_ptr()), C.c_void_p(stream.cuda_stream))
+    assert rc == 0
+    stream.synchronize()
+    assert pool.get(pool.USED_MEM_HIGH) >= used0 + 3 * 8 * A.n
+    assert torch.equal(y, y2)
