@@ -300,6 +300,38 @@ int32_t ppg_solve_batched(int32_t nsys, const ppg_csr* As, int32_t nrhs,
 int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r,
                             const double* b, double* stch, void* stream);
 
+/* Outcome of ppg_build_poly_checked. */
+typedef struct ppg_poly_check {
+    int32_t d_requested;   /* degree asked for */
+    int32_t d_chosen;      /* original degree of the returned polynomial */
+    int32_t n_tried;       /* degrees checked, the requested one first */
+    int32_t pad_;
+    double  stch;          /* StCh of the returned polynomial */
+    double  stch_first;    /* StCh at the first degree checked */
+} ppg_poly_check;
+
+/* Algorithm 4 step 1 followed by the stability check of Section 3.5, which
+ * the paper applies once the polynomial is determined and before the
+ * solve, lowering the degree when instability is predicted.  The degree-d
+ * polynomial is built as by ppg_build_poly; then, with the unit vector
+ * u = b / ||b|| (u = v0 / ||v0|| when b is NULL), StCh = ||(u - A p(A) u) -
+ * pi(A) u|| is computed (Algorithms 3 and 1, as ppg_stability_check).
+ * While StCh > stch_tol and the degree is above d_min, the degree is
+ * halved (d' = max(d_min, d / 2); the paper does not say by how much) and
+ * the roots of GMRES(d') from the same v0 -- the leading (d'+1) x d' block
+ * of the same Arnoldi run, so no further Arnoldi steps -- are formed,
+ * ordered, augmented by Algorithm 2 (opts) and checked in turn.  `out`
+ * receives the last polynomial checked; info (nullable) the degrees and
+ * StCh values.  A StCh that overflows counts as above any tolerance.  If
+ * the floor is reached with StCh still above stch_tol the call returns
+ * PPG_OK with info->stch > stch_tol.  A PPG_F64; v0, b device double.
+ * Returns PPG_OK, PPG_LUCKY_BREAKDOWN (as ppg_build_poly) or an error.
+ * Synchronises. */
+int32_t ppg_build_poly_checked(const ppg_csr* A, int32_t d, const double* v0,
+                               const double* b, double stch_tol, int32_t d_min,
+                               const ppg_opts* opts, ppg_roots* out,
+                               ppg_poly_check* info, void* stream);
+
 /* Transposed CSR of A (for the adjoint solve with A^T): rowptr_t [n+1],
  * colind_t [nnz], vals_t [nnz] in A's dtype, all device, caller-owned.
  * perm (nullable, [nnz]) receives for each entry of A^T the index of the

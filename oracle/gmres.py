@@ -270,6 +270,30 @@ def stability_check(A, roots: np.ndarray, b: np.ndarray) -> float:
     return float(np.linalg.norm(r1 - r2))
 
 
+def build_poly_checked(A, d: int, v0: np.ndarray, b: Optional[np.ndarray], tol: float,
+                       d_min: int = 1, stability: bool = True):
+    """The polynomial with the stability check of Section 3.5 applied before
+    the solve: build the degree-d polynomial from v0 (Algorithm 4 step 1),
+    compute StCh with the unit vector b / ||b|| (v0 / ||v0|| when b is None),
+    and while StCh > tol and the degree is above d_min, lower the degree and
+    check again.  The paper says only that the degree "can be lowered"; the
+    reading taken here halves it, d <- max(d_min, d // 2), and the lower-degree
+    polynomial is GMRES(d) from the same v0.  Returns (Poly, tried) with
+    tried = [(original degree, StCh), ...] largest degree first."""
+    from .poly import build_poly
+    u = v0 if b is None else b
+    u = u / np.linalg.norm(u)
+    tried = []
+    deg = d
+    while True:
+        pp = build_poly(A, deg, v0, stability=stability)
+        s = stability_check(A, pp.roots, u)
+        tried.append((pp.d, s))
+        if s <= tol or pp.d <= d_min:
+            return pp, tried
+        deg = max(d_min, pp.d // 2)
+
+
 def adjoint_grads(A, AT, roots, x: np.ndarray, gx: np.ndarray, m: int,
                   tol: float, rowptr: np.ndarray, colind: np.ndarray,
                   max_cycles: int = 1000):

@@ -55,6 +55,14 @@ class ppg_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class ppg_poly_check(C.Structure):
+    _fields_ = [("d_requested", c_i32), ("d_chosen", c_i32), ("n_tried", c_i32),
+                ("pad_", c_i32), ("stch", c_f64), ("stch_first", c_f64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
 class PPGError(RuntimeError):
     def __init__(self, code, where):
         msg = lib.ppg_strerror(code).decode()
@@ -83,6 +91,9 @@ def _load():
         "ppg_csr_validate_host": (c_i32, [c_i32, c_i32, c_vp, c_vp]),
         "ppg_build_poly": (c_i32, [C.POINTER(ppg_csr), c_i32, c_vp, C.POINTER(ppg_opts),
                                    C.POINTER(ppg_roots), P_F64, c_vp]),
+        "ppg_build_poly_checked": (c_i32, [C.POINTER(ppg_csr), c_i32, c_vp, c_vp, c_f64, c_i32,
+                                           C.POINTER(ppg_opts), C.POINTER(ppg_roots),
+                                           C.POINTER(ppg_poly_check), c_vp]),
         "ppg_apply_poly": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
         "ppg_apply_phi": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
         "ppg_apply_poly_noalloc": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp,
@@ -128,6 +139,7 @@ EXPORTS = (
     "ppg_spmv", "ppg_solve", "ppg_solve_flex", "ppg_stability_check",
     "ppg_csr_transpose", "ppg_adjoint_vals_grad", "ppg_apply_poly_noalloc",
     "ppg_solve_batched", "ppg_build_poly_composite", "ppg_solve_double", "ppg_solve_chpoly",
+    "ppg_build_poly_checked",
 )
 
 

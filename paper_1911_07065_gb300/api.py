@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from ._binding import (PPG_F32, PPG_F64, Roots, check, default_opts, lib, ppg_roots,
-                       ppg_csr, ppg_stats, csr_validate_host, _dp)
+                       ppg_csr, ppg_poly_check, ppg_stats, csr_validate_host, _dp)
 
 
 def _stream(stream=None):
@@ -98,6 +98,30 @@ def build_poly(A: CSR, d: int, v0: torch.Tensor, stability_control: bool = True,
     check(rc, "ppg_build_poly")
     Hbar = H.reshape(d, d + 1).T.copy()
     return (r, Hbar) if return_hbar else r
+
+
+def build_poly_checked(A: CSR, d: int, v0: torch.Tensor, stch_tol: float,
+                       b: Optional[torch.Tensor] = None, d_min: int = 1,
+                       stability_control: bool = True, capacity: Optional[int] = None,
+                       stream=None):
+    """Algorithm 4 step 1 with the stability check of Section 3.5 (degree
+    halved while StCh > stch_tol, down to d_min).  Returns (Roots, info) with
+    info = {d_requested, d_chosen, n_tried, stch, stch_first}."""
+    _need_cuda(v0)
+    if v0.dtype != torch.float64 or (b is not None and b.dtype != torch.float64):
+        raise ValueError("v0 and b must be float64")
+    cap = capacity or max(16, 4 * d)
+    r = Roots(cap)
+    info = ppg_poly_check()
+    o = default_opts(stability_control=int(bool(stability_control)))
+    rc = lib.ppg_build_poly_checked(A.ref(), d, _ptr(v0), _ptr(b) if b is not None else None,
+                                    float(stch_tol), int(d_min), C.byref(o), r.ref(),
+                                    C.byref(info), _stream(stream))
+    if rc == -6 and capacity is None:
+        return build_poly_checked(A, d, v0, stch_tol, b, d_min, stability_control,
+                                  r.s.n_total + 8, stream)
+    check(rc, "ppg_build_poly_checked")
+    return r, info.as_dict()
 
 
 def apply_poly(A: CSR, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor] = None,

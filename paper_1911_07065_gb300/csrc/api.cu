@@ -4,6 +4,7 @@
 // step 2, plus the FP32-inner flexible form), the stability check of
 // Section 3.5 and the adjoint helpers.
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1220,13 +1221,15 @@ int32_t ppg_solve_chpoly(const ppg_csr* A, int32_t d, const double* b, double* x
     return rc;
 }
 
-int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r, const double* b,
-                            double* stch, void* stream) {
-    PPG_TRY(check_csr(A, PPG_F64));
-    PPG_TRY(check_roots(r));
-    if (!b || !stch) return PPG_ERR_ARG;
+}  // extern "C"
+
+namespace ppg {
+
+// StCh of Section 3.5 with the device vector b: ||r1 - r2||, r1 = b - A p(A) b
+// (Algorithm 3 and one SpMV), r2 = pi(A) b (Algorithm 1).  Writes *stch.
+static int32_t stch_core(const ppg_csr* A, const ppg_roots* r, const double* b, double* stch,
+                         cudaStream_t s) {
     PPG_TRY(setup_device_pool());
-    cudaStream_t s = (cudaStream_t)stream;
     const int32_t n = A->n;
     const int d = r->n_total;
     Arena ar;
@@ -1273,6 +1276,76 @@ int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r, const double* 
     PPG_CUDA(cudaStreamSynchronize(s));
     *stch = sc[3];
     return std::isfinite(sc[3]) ? PPG_OK : PPG_ERR_NONFINITE;
+}
+
+}  // namespace ppg
+
+extern "C" {
+
+int32_t ppg_stability_check(const ppg_csr* A, const ppg_roots* r, const double* b,
+                            double* stch, void* stream) {
+    PPG_TRY(check_csr(A, PPG_F64));
+    PPG_TRY(check_roots(r));
+    if (!b || !stch) return PPG_ERR_ARG;
+    return stch_core(A, r, b, stch, (cudaStream_t)stream);
+}
+
+int32_t ppg_build_poly_checked(const ppg_csr* A, int32_t d, const double* v0, const double* b,
+                               double stch_tol, int32_t d_min, const ppg_opts* opts,
+                               ppg_roots* out, ppg_poly_check* info, void* stream) {
+    PPG_TRY(check_csr(A, PPG_F64));
+    if (!v0 || !out || d < 1 || d + 1 > ORTHO_MAXC || !(stch_tol >= 0.0)) return PPG_ERR_ARG;
+    ppg_opts o;
+    ppg_default_opts(&o);
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ldh = d + 1;
+    std::vector<double> H((size_t)ldh * d, 0.0);
+    // Algorithm 4 step 1 at the requested degree; its Hessenberg matrix also
+    // gives every lower degree (GMRES(d') from v0 is its leading block)
+    const int32_t built = build_core(A, d, v0, o, nullptr, out, H.data(), s);
+    if (built < 0) return built;
+    // the check vector u = b / ||b|| (v0 / ||v0|| when b is NULL)
+    const int32_t n = A->n;
+    Arena ar;
+    double *u = nullptr, *part = nullptr, *scal = nullptr;
+    ar.add(&u, n);
+    ar.add(&part, (size_t)spmv_grid_blocks(n) + 1024);
+    ar.add(&scal, 8);
+    PPG_TRY(ar.alloc(s));
+    struct Guard { Arena& a; cudaStream_t s; ~Guard() { a.release(s); } } guard{ar, s};
+    const double* src = b ? b : v0;
+    int nparts = 0;
+    PPG_TRY(launch_norm2_part(src, n, part, s, &nparts));
+    PPG_TRY(launch_reduce_norm(part, nparts, scal, nullptr, s));
+    PPG_TRY(launch_scale(src, u, n, scal + 4, s));
+    double sc[8];
+    PPG_CUDA(cudaMemcpyAsync(sc, scal, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    PPG_CUDA(cudaStreamSynchronize(s));
+    if (!(sc[3] > 0.0) || !std::isfinite(sc[3])) return PPG_ERR_ARG;
+    const int floor_d = std::max(1, std::min<int>(d_min, out->n_orig));
+    ppg_poly_check pc{};
+    pc.d_requested = d;
+    int deg = out->n_orig;
+    for (;;) {
+        double stch = 0.0;
+        const int32_t rc = stch_core(A, out, u, &stch, s);
+        if (rc == PPG_ERR_NONFINITE) {
+            stch = HUGE_VAL;   // overflowed: as unstable as it gets
+        } else if (rc < 0) {
+            return rc;
+        }
+        pc.n_tried += 1;
+        if (pc.n_tried == 1) pc.stch_first = stch;
+        pc.stch = stch;
+        pc.d_chosen = deg;
+        if (stch <= stch_tol || deg <= floor_d) break;
+        deg = std::max(floor_d, deg / 2);
+        const int32_t rr = ppg_roots_from_hessenberg(H.data(), ldh, deg, &o, out);
+        if (rr < 0) return rr;
+    }
+    if (info) *info = pc;
+    return built;   // PPG_OK or PPG_LUCKY_BREAKDOWN
 }
 
 int32_t ppg_csr_transpose(const ppg_csr* A, int32_t* rowptr_t, int32_t* colind_t, void* vals_t,

@@ -269,6 +269,56 @@ def test_stability_check_matches_oracle(env):
             assert s_orc > 1e-4 and s_gpu > 1e-4
 
 
+def test_build_poly_checked_lowers_the_degree_like_the_oracle(env):
+    """Section 3.5 inside the construction: on the outlier matrix without
+    root adding, StCh rejects degrees 40, 20 and 10 and keeps 5 on both sides;
+    each StCh the device computes is within a factor 100 of the oracle's
+    (StCh measures rounding, which the two sides do in different orders; the
+    paper itself expects only order-of-magnitude agreement), the kept roots
+    match the oracle's within 1e-10, and with root adding the degree-40
+    polynomial passes at once."""
+    p, torch = env
+    A = synth.cd2d(20, 0.5)
+    k = A.rowptr[137] + 2
+    assert A.colind[k] == 137
+    A.vals[k] = 1e4
+    As = A.to_scipy()
+    v0 = np.random.default_rng(1).standard_normal(A.n)
+    bb = np.random.default_rng(2).standard_normal(A.n)
+    Ad = dev_csr(p, torch, A)
+    tol = 1e-10
+    orc, tried = gmres.build_poly_checked(As, 40, v0, bb, tol, d_min=2, stability=False)
+    R, info = p.build_poly_checked(Ad, 40, to_dev(torch, v0), tol, b=to_dev(torch, bb),
+                                   d_min=2, stability_control=False)
+    assert info["d_requested"] == 40
+    assert info["n_tried"] == len(tried) == 4
+    assert info["d_chosen"] == orc.d == 5 == R.n_orig
+    assert info["stch"] <= tol
+    # first degree: hugely unstable on both sides; kept degree: rounding level
+    assert tried[0][1] > 1e6 and info["stch_first"] > 1e6
+    assert tried[-1][1] <= 1e-12 and info["stch"] <= 1e-12
+    # a rejected degree whose StCh is moderate (degree 10, about 2e-3): the
+    # same roots on both sides, so only the rounding of Algorithms 1 and 3
+    # differs, and StCh agrees within a factor 100
+    deg10 = poly.build_poly(As, 10, v0, stability=False).roots
+    s_orc = gmres.stability_check(As, deg10, bb / np.linalg.norm(bb))
+    s_dev = p.stability_check(Ad, p.Roots.from_complex(deg10),
+                              to_dev(torch, bb / np.linalg.norm(bb)))
+    assert 1e-6 < s_orc < 1.0
+    assert abs(np.log10(s_dev) - np.log10(s_orc)) <= 2.0, (s_dev, s_orc)
+    got = R.complex()
+    assert got.size == orc.roots.size
+    assert np.max(np.abs(np.sort_complex(got) - np.sort_complex(orc.roots))) <= \
+        1e-10 * np.max(np.abs(orc.roots))
+    # the lowered polynomial is the one ppg_build_poly gives at that degree
+    R5 = p.build_poly(Ad, 5, to_dev(torch, v0), stability_control=False)
+    assert np.array_equal(R5.complex(), got)
+    # with Algorithm 2's added roots the requested degree passes
+    R40, info40 = p.build_poly_checked(Ad, 40, to_dev(torch, v0), tol, b=to_dev(torch, bb))
+    assert info40["n_tried"] == 1 and info40["d_chosen"] == 40 and R40.n_added >= 1
+    assert info40["stch"] <= tol
+
+
 def test_transpose_and_adjoint_gradient(env):
     p, torch = env
     N = 24

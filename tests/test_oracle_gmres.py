@@ -142,6 +142,53 @@ def test_stability_check_small_for_stable_and_large_for_unstable():
     assert s_good < s_bad
 
 
+def _outlier_cd2d(value=1e4):
+    """20 x 20 convection-diffusion with one outlying diagonal entry: the
+    high-degree GMRES polynomial without root adding is unstable on it."""
+    A = synth.cd2d(20, 0.5)
+    k = A.rowptr[137] + 2
+    assert A.colind[k] == 137
+    A.vals[k] = value
+    return A
+
+
+def test_checked_construction_lowers_the_degree_until_stch_passes():
+    """Section 3.5: the check runs once the polynomial is built and before
+    the solve; the degree is lowered (halved, the reading taken) while StCh
+    is above tol.  Pins: with a loose tol nothing changes; every degree it
+    rejects has StCh above tol and makes PP-GMRES fail to reach tol (the
+    instability is detected before the solve), the degree it keeps has StCh
+    at or below tol and PP-GMRES converges with it; the kept polynomial is
+    GMRES(d') from the same v0."""
+    A = _outlier_cd2d()
+    As = A.to_scipy()
+    v0 = np.random.default_rng(1).standard_normal(A.n)
+    b = np.random.default_rng(2).standard_normal(A.n)
+    b /= np.linalg.norm(b)
+    loose, tried = gmres.build_poly_checked(As, 40, v0, b, 1e300, stability=False)
+    assert tried[0][0] == 40 and len(tried) == 1
+    assert np.array_equal(loose.roots, poly.build_poly(As, 40, v0, stability=False).roots)
+    tol = 1e-10
+    pp, tried = gmres.build_poly_checked(As, 40, v0, b, tol, d_min=2, stability=False)
+    degs = [t[0] for t in tried]
+    assert degs == [40, 20, 10, 5]
+    assert all(s > tol for _, s in tried[:-1]) and tried[-1][1] <= tol
+    assert pp.d == 5
+    assert np.array_equal(pp.roots, poly.build_poly(As, 5, v0, stability=False).roots)
+    for deg, _ in tried[:-1]:
+        bad = poly.build_poly(As, deg, v0, stability=False)
+        _, st = gmres.pp_gmres(As, bad.roots, b, 50, tol, max_cycles=10)
+        assert not st.converged
+    _, st = gmres.pp_gmres(As, pp.roots, b, 50, tol, max_cycles=50)
+    assert st.converged and st.true_relres <= tol
+    # with root adding (Algorithm 2) the degree-40 polynomial passes at once
+    good, tried = gmres.build_poly_checked(As, 40, v0, b, tol, stability=True)
+    assert len(tried) == 1 and good.n_added >= 1
+    # the floor stops the lowering even when StCh stays above tol
+    _, tried = gmres.build_poly_checked(As, 40, v0, b, 1e-30, d_min=20, stability=False)
+    assert [t[0] for t in tried] == [40, 20]
+
+
 def test_adjoint_matches_dense_solve_and_finite_differences():
     N = 10
     fld = synth.smooth_field(N, synth.streams(105)[2])
