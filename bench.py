@@ -166,14 +166,43 @@ def oracle_sample(n_iters: int = 2):
             "degree": int(pp.roots.size)}
 
 
-def _run_oracle_subprocess(n_iters):
+def oracle_c1():
+    """The oracle's full solve of the 50 x 50 workload (build_poly d = 10 and
+    PP(10)-GMRES(50) to 1e-8), timed once after one untimed run."""
+    import numpy as np
+    import synth
+    from oracle import gmres, poly
+
+    P = synth.problem("cd2d_50")
+    As = P.A.to_scipy()
+
+    def run():
+        pp = poly.build_poly(As, P.d, P.v0)
+        x, st = gmres.pp_gmres(As, pp.roots, P.b, P.m, P.tol)
+        return pp, x, st
+    run()
+    t0 = time.perf_counter()
+    pp, x, st = run()
+    t = time.perf_counter() - t0
+    return {"solve_ms": 1e3 * t, "iters": st.iters, "cycles": st.cycles,
+            "degree": int(pp.roots.size),
+            "true_relres": float(np.linalg.norm(P.b - As @ x) / np.linalg.norm(P.b))}
+
+
+def _oracle_cores():
+    return os.cpu_count() or 1
+
+
+def _run_oracle_subprocess(n_iters, mode="--oracle-sample"):
+    """Run the oracle in a child process with BLAS threads on all host cores
+    (SciPy's sparse matvec itself is single-threaded)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
-                        str(n_iters)], capture_output=True, text=True, env=env, cwd=ROOT)
+        env[k] = str(_oracle_cores())
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), mode, str(n_iters)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
@@ -240,7 +269,8 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": 1000000, "nnz": 4996000, "d": 40, "m": 50,
                    "tol": 1e-10, "extrapolated": True},
-        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": _oracle_cores(),
+                         "kind": "oracle",
                          "sample": "oracle build_poly(d=40) + %d PP-GMRES iterations + one "
                                    "restart update per step, extrapolated to %d iterations / "
                                    "%d restarts" % (args.oracle_iters, iters, cycles)},
@@ -384,10 +414,11 @@ def run_ours(args, rank, local, world):
         s = _run_oracle_subprocess(args.oracle_iters)
         v = _extrapolate(s, st["iters"], st["cycles"])
         line["cpu_baseline"] = {
-            "value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "value": round(v, 1), "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
             "sample": "oracle build_poly(d=40) + %d PP-GMRES(50) iterations + one restart "
                       "update on this workload, extrapolated to this run's %d iterations / "
-                      "%d restarts (oracle build %.2f s, %.3f s/iteration)"
+                      "%d restarts (oracle build %.2f s, %.3f s/iteration; BLAS threads on "
+                      "all host cores, SciPy sparse matvec single-threaded)"
                       % (s["n_iters"], st["iters"], st["cycles"], s["t_build"], s["t_iter"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -459,6 +490,64 @@ def spmv_yardstick(device, A64, A32, n):
     return out
 
 
+def _median_ms(torch, fn, reps=10, warm=3):
+    """Median CUDA-event time of fn() on the current stream over `reps` runs
+    after `warm` untimed runs."""
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def measure_c1(device):
+    """The 50 x 50 workload (n = 2,500, latency-bound): microseconds per
+    p(A) v and phi(A) v and per solve (median of 10 after 3 warm-ups), with
+    the oracle's full solve on the host cores beside it."""
+    import numpy as np
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+    import synth
+
+    P = synth.problem("cd2d_50")
+    A = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
+    b = torch.from_numpy(P.b).to(device)
+    v0 = torch.from_numpy(P.v0).to(device)
+    R = ppg.build_poly(A, P.d, v0)
+    v = torch.from_numpy(np.random.default_rng(0).standard_normal(P.A.n)).to(device)
+    y = torch.empty_like(v)
+    x = torch.empty_like(b)
+    t_p = _median_ms(torch, lambda: ppg.apply_poly(A, R, v, out=y))
+    t_phi = _median_ms(torch, lambda: ppg.apply_phi(A, R, v, out=y))
+    t_solve = _median_ms(torch, lambda: ppg.solve(A, b, P.m, P.tol, roots=R, out=x))
+
+    def build_and_solve():
+        Rb = ppg.build_poly(A, P.d, v0)
+        return ppg.solve(A, b, P.m, P.tol, roots=Rb, out=x)
+    t_all = _median_ms(torch, build_and_solve)
+    _, st = ppg.solve(A, b, P.m, P.tol, roots=R, out=x)
+    rel = float(np.linalg.norm(P.b - P.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(P.b))
+    orc = _run_oracle_subprocess(0, "--oracle-c1")
+    return {"n": P.A.n, "nnz": P.A.nnz, "degree": R.n_total,
+            "p_apply_us": round(1e3 * t_p, 2), "phi_apply_us": round(1e3 * t_phi, 2),
+            "solve_us": round(1e3 * t_solve, 1), "build_and_solve_us": round(1e3 * t_all, 1),
+            "iters": st["iters"], "cycles": st["cycles"], "true_relres": rel,
+            "timing": "CUDA events, median of 10 after 3 warm-ups",
+            "oracle": {"solve_ms": round(orc["solve_ms"], 2), "iters": orc["iters"],
+                       "cycles": orc["cycles"], "true_relres": orc["true_relres"],
+                       "cores": _oracle_cores(), "kind": "oracle, full solve (build + PP-GMRES)"}}
+
+
 def measure_forms(device):
     """The three forms beside the plain FP64 method, each against the plain
     FP64 PP-GMRES on the same GPU at relative residual 1e-10 (one run each,
@@ -469,7 +558,7 @@ def measure_forms(device):
     import paper_1911_07065_gb300 as ppg
     import synth
 
-    out = {}
+    out = {"c1_cd2d_50": measure_c1(device)}
     # precision form: 3-D 160^3, FP32 p(A) inside FP64 FGMRES(50) vs full FP64
     P = synth.problem("cd3d_160")
     A64 = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
@@ -644,12 +733,16 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=200)
     ap.add_argument("--ref-cycles", type=int, default=4)
     ap.add_argument("--oracle-sample", type=int, default=None)
+    ap.add_argument("--oracle-c1", type=int, default=None)
     ap.add_argument("--profile-case", default=None)
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args.profile_case)
     if args.oracle_sample is not None:
         print(json.dumps(oracle_sample(args.oracle_sample)))
+        return 0
+    if args.oracle_c1 is not None:
+        print(json.dumps(oracle_c1()))
         return 0
     rank, local, world = _dist_env()
     if args.impl == "reference":
