@@ -51,6 +51,8 @@ extern "C" {
 #define PPG_ERR_EIG          -7   /* Hessenberg QR did not converge */
 #define PPG_ERR_NOMEM        -8   /* device scratch allocation failed */
 #define PPG_ERR_TOO_LARGE    -9   /* n above PPG_NOALLOC_MAX_N (ppg_apply_poly_noalloc) */
+#define PPG_ERR_TIMEOUT     -10   /* a bounded wait inside a kernel gave up (data staging or
+                                     a grid-wide barrier did not complete in time) */
 
 /* Largest n that ppg_apply_poly_noalloc accepts (its fixed work area). */
 #define PPG_NOALLOC_MAX_N 1048576

@@ -24,7 +24,7 @@ STATUS = {
     0: "PPG_OK", 1: "PPG_NOT_CONVERGED", 2: "PPG_LUCKY_BREAKDOWN",
     -1: "PPG_ERR_ARG", -2: "PPG_ERR_CSR", -3: "PPG_ERR_SINGULAR_H",
     -4: "PPG_ERR_NONFINITE", -5: "PPG_ERR_CUDA", -6: "PPG_ERR_CAPACITY",
-    -7: "PPG_ERR_EIG", -8: "PPG_ERR_NOMEM", -9: "PPG_ERR_TOO_LARGE",
+    -7: "PPG_ERR_EIG", -8: "PPG_ERR_NOMEM", -9: "PPG_ERR_TOO_LARGE", -10: "PPG_ERR_TIMEOUT",
 }
 NOALLOC_MAX_N = 1048576
 

@@ -219,12 +219,13 @@ int device_sm_count() {
 static int64_t pad_ld(int32_t n) { return ((int64_t)n + 63) / 64 * 64; }
 
 // Pinned host buffer for the per-step status read (one per host thread,
-// allocated on first use and kept for the life of the process).
+// allocated on first use and kept for the life of the process): 8 doubles
+// of GmresState::scal, then the CGS2 error flag at element 8.
 static int32_t status_buffer(double** out) {
     static thread_local double* buf = nullptr;
     if (!buf) {
         void* p = nullptr;
-        PPG_CUDA(cudaMallocHost(&p, 8 * sizeof(double)));
+        PPG_CUDA(cudaMallocHost(&p, 16 * sizeof(double)));
         buf = (double*)p;
     }
     *out = buf;
@@ -316,14 +317,28 @@ struct SolveCore {
     ppg_stats st{};
 };
 
+// CGS2 of basis column j + 1 (w) against columns 0..j: h1 = V^T w; w -= V h1;
+// h2 = V^T w; w -= V h2 with ||w||^2.  The middle two passes run fused (one
+// pass over V) when the basis layout allows it.
 static int32_t cgs2_column(SolveCore& c, int j, double* w, bool with_self, EventPair* ev) {
     const int32_t n = c.A64->n;
     if (ev) ev->start(c.s);
     PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, with_self, c.ows.h1, c.ows, c.s));
-    PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h1, false, nullptr, c.ows, c.s));
-    PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, false, c.ows.h2, c.ows, c.s));
+    if (cgs_fused_ok(c.V, c.ldv, j + 1, w)) {
+        PPG_TRY(launch_cgs_sub_dot(c.V, c.ldv, j + 1, w, n, c.ows.h1, c.ows.h2, c.ows, c.s));
+    } else {
+        PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h1, false, nullptr, c.ows,
+                                  c.s));
+        PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, false, c.ows.h2, c.ows, c.s));
+    }
     PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h2, true, c.ows.nrm, c.ows, c.s));
     return PPG_OK;
+}
+
+// the error flag of the fused CGS2 pass (a staging wait gave up); `flag`
+// is host memory filled by a copy the caller has synchronised
+static int32_t ortho_status(const unsigned* flag) {
+    return *flag != 0u ? PPG_ERR_TIMEOUT : PPG_OK;
 }
 
 // Algorithm 4 step 1 with operator M = A, or M = phi_inner(A) when inner is
@@ -401,7 +416,11 @@ static int32_t build_core(const ppg_csr* A, int d, const double* v0, const ppg_o
     PPG_CUDA(cudaMemcpyAsync(H.data(), c.gs.Hraw, sizeof(double) * ldh * d,
                              cudaMemcpyDeviceToHost, s));
     PPG_CUDA(cudaMemcpyAsync(sc.data(), c.gs.scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    unsigned oflag = 0;
+    PPG_CUDA(cudaMemcpyAsync(&oflag, c.ows.counter + 3, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             s));
     PPG_CUDA(cudaStreamSynchronize(s));
+    PPG_TRY(ortho_status(&oflag));
     if (Hbar_host) std::memcpy(Hbar_host, H.data(), sizeof(double) * ldh * d);
     if (!std::isfinite(sc[3]) || sc[3] == 0.0) return PPG_ERR_ARG;   // v0 zero or non-finite
     const bool brk = sc[5] != 0.0;
@@ -699,7 +718,10 @@ static int32_t run_solve(SolveCore& c) {
         c.st.mvps += 1;
         c.st.dots += 1;
         PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PPG_CUDA(cudaMemcpyAsync(scal_h + 8, c.ows.counter + 3, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, s));
         PPG_CUDA(cudaStreamSynchronize(s));
+        PPG_TRY(ortho_status(reinterpret_cast<const unsigned*>(scal_h + 8)));
         if (pp && !c.flex) c.st.poly_ms += ev_restart.ms();
         beta = scal_h[3];
         if (!std::isfinite(beta)) return PPG_ERR_NONFINITE;
@@ -928,7 +950,10 @@ static int32_t run_solve_ext(SolveCore& c, const ppg_roots* inner, int rebuild_d
         c.st.mvps += dM;
         c.st.dots += 1;
         PPG_CUDA(cudaMemcpyAsync(scal_h, c.gs.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PPG_CUDA(cudaMemcpyAsync(scal_h + 8, c.ows.counter + 3, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, s));
         PPG_CUDA(cudaStreamSynchronize(s));
+        PPG_TRY(ortho_status(reinterpret_cast<const unsigned*>(scal_h + 8)));
         beta = scal_h[3];
         if (!std::isfinite(beta)) return PPG_ERR_NONFINITE;
         c.st.true_relres = beta / bnorm;
@@ -978,6 +1003,7 @@ const char* ppg_strerror(int32_t code) {
         case PPG_ERR_EIG: return "Hessenberg QR did not converge";
         case PPG_ERR_NOMEM: return "device scratch allocation failed";
         case PPG_ERR_TOO_LARGE: return "n exceeds PPG_NOALLOC_MAX_N (1048576), the fixed work area of ppg_apply_poly_noalloc";
+        case PPG_ERR_TIMEOUT: return "a bounded wait inside a kernel gave up (staging or grid barrier did not complete)";
         default: return "unknown status";
     }
 }

@@ -269,6 +269,231 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     }
 }
 
+// ---------------------------------------------------------------------------
+// CGS2 passes 2 and 3 in one pass over V:  w -= V h1, then h2 = V^T w of the
+// updated w.  The update of a row needs only that row of V, so a tile of
+// rows is staged in shared memory once and serves both products: 3/4 of the
+// unfused passes' bytes, the same FP64 multiply-adds.
+//
+// Tiles of SD_R rows x ncol columns (plus the tile of w) move from HBM to
+// shared memory with one bulk copy per column (the TMA engine; column c of
+// the tile is one contiguous 1 KB range of the column-major basis), double
+// buffered on two mbarriers, so the threads issue no load instructions for
+// V at all.  Phase 1: thread (row pair p, column group q) sums V[r, c] h1[c]
+// over its quarter of the columns; the four partial sums of a row are added
+// in a fixed order and w' = w - s is written back.  Phase 2: warp k owns
+// columns k, k + 8, ... (at most SD_MAXC / 8 per warp) and each lane adds
+// V[r, c] w'[r] for four rows of the tile into per-column accumulators that
+// persist across the CTA's tiles.  Per-CTA partial sums are reduced by the
+// last CTA in a fixed order (deterministic).
+//
+// Every wait on an mbarrier is bounded; a CTA whose copies do not arrive
+// sets *err, waits (bounded) for the copies it issued, and returns.
+// ---------------------------------------------------------------------------
+
+constexpr int SD_R = 128;                 // rows per tile
+constexpr int SD_MAXC = 56;               // columns (7 per warp)
+constexpr int SD_CPW = SD_MAXC / ORTHO_WARPS;
+constexpr uint32_t SD_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for phase `parity` of the mbarrier at `bar`
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < SD_SPIN_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__global__ void __launch_bounds__(ORTHO_THREADS)
+k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
+          const double* __restrict__ h1, double* part, unsigned* counter, double* hout,
+          unsigned* err) {
+    extern __shared__ __align__(128) double sd_stage[];   // 2 x (ncol + 1) x SD_R
+    __shared__ double sh[SD_MAXC];
+    __shared__ __align__(16) double spart[4][SD_R];
+    __shared__ __align__(16) double ws[SD_R];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t stage_elems = (int64_t)(ncol + 1) * SD_R;   // w's tile is slot ncol
+    const int ntiles = (int)(((int64_t)n + SD_R - 1) / SD_R);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();   // h1 and w come from the kernels before this one
+    for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = h1[c];
+    __syncthreads();
+
+    // thread 0: tile t into stage st (rows up to the padded column length,
+    // a multiple of 64 rows, so every copy is a whole number of 16 bytes)
+    auto issue = [&](int t, int st) {
+        const int64_t r0 = (int64_t)t * SD_R;
+        const int64_t rows = min((int64_t)SD_R, ldv - r0);
+        const uint32_t bytes = (uint32_t)(rows * 8);
+        const uint32_t b = smem_u32(&bar[st]);
+        double* dst = sd_stage + st * stage_elems;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
+                     "r"(bytes * (uint32_t)(ncol + 1))
+                     : "memory");
+        for (int c = 0; c <= ncol; ++c) {
+            const double* src = (c < ncol ? V + c * ldv : w) + r0;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                ::"r"(smem_u32(dst + c * SD_R)), "l"(src), "r"(bytes), "r"(b)
+                : "memory");
+        }
+    };
+    const int first = blockIdx.x;
+    const int step = gridDim.x;
+    if (tid == 0) {
+        if (first < ntiles) issue(first, 0);
+        if (first + step < ntiles) issue(first + step, 1);
+    }
+
+    double acc[SD_CPW];
+#pragma unroll
+    for (int k = 0; k < SD_CPW; ++k) acc[k] = 0.0;
+    const int p = tid & 63, q = tid >> 6;   // phase 1: row pair, column group
+    int k_local = 0;
+    bool ok = true;
+    for (int t = first; t < ntiles; t += step, ++k_local) {
+        const int st = k_local & 1;
+        const uint32_t parity = (uint32_t)((k_local >> 1) & 1);
+        const bool mine = mbar_wait_bounded(smem_u32(&bar[st]), parity);
+        if (!__syncthreads_and(mine)) {
+            ok = false;
+            break;
+        }
+        const double* S = sd_stage + st * stage_elems;
+        const int64_t r0 = (int64_t)t * SD_R;
+        // phase 1: partial sums of (V h1)[r] over columns q, q + 4, ...
+        {
+            double s0 = 0.0, s1 = 0.0;
+            for (int c = q; c < ncol; c += 4) {
+                const double2 v = *reinterpret_cast<const double2*>(S + c * SD_R + 2 * p);
+                const double hc = sh[c];
+                s0 = fma(v.x, hc, s0);
+                s1 = fma(v.y, hc, s1);
+            }
+            spart[q][2 * p] = s0;
+            spart[q][2 * p + 1] = s1;
+        }
+        __syncthreads();
+        if (tid < 64) {
+            const int r = 2 * tid;
+            const double2 wv = *reinterpret_cast<const double2*>(S + ncol * SD_R + r);
+            const double sa = ((spart[0][r] + spart[1][r]) + spart[2][r]) + spart[3][r];
+            const double sb =
+                ((spart[0][r + 1] + spart[1][r + 1]) + spart[2][r + 1]) + spart[3][r + 1];
+            const int64_t g = r0 + r;
+            double2 o;
+            o.x = g < n ? wv.x - sa : 0.0;
+            o.y = g + 1 < n ? wv.y - sb : 0.0;
+            *reinterpret_cast<double2*>(ws + r) = o;
+            if (g + 1 < n) {
+                *reinterpret_cast<double2*>(w + g) = o;
+            } else if (g < n) {
+                w[g] = o.x;
+            }
+        }
+        __syncthreads();
+        // phase 2: this warp's columns against the tile's w' (rows 2 lane,
+        // 2 lane + 1, 64 + 2 lane, 65 + 2 lane).  Rows at or past n hold the
+        // basis's padding (never written, possibly not finite): in the last,
+        // partial tile they are replaced by zeros before the multiply-adds.
+        {
+            const double2 wa = *reinterpret_cast<const double2*>(ws + 2 * lane);
+            const double2 wb = *reinterpret_cast<const double2*>(ws + 64 + 2 * lane);
+            if (r0 + SD_R <= n) {
+#pragma unroll
+                for (int k = 0; k < SD_CPW; ++k) {
+                    const int c = warp + k * ORTHO_WARPS;
+                    if (c < ncol) {   // uniform over the warp: no FMA for a missing column
+                        const double2 va =
+                            *reinterpret_cast<const double2*>(S + c * SD_R + 2 * lane);
+                        const double2 vb =
+                            *reinterpret_cast<const double2*>(S + c * SD_R + 64 + 2 * lane);
+                        acc[k] = fma(va.x, wa.x, acc[k]);
+                        acc[k] = fma(va.y, wa.y, acc[k]);
+                        acc[k] = fma(vb.x, wb.x, acc[k]);
+                        acc[k] = fma(vb.y, wb.y, acc[k]);
+                    }
+                }
+            } else {
+                const int64_t ra = r0 + 2 * lane, rb = r0 + 64 + 2 * lane;
+#pragma unroll
+                for (int k = 0; k < SD_CPW; ++k) {
+                    const int c = warp + k * ORTHO_WARPS;
+                    if (c < ncol) {
+                        double2 va = *reinterpret_cast<const double2*>(S + c * SD_R + 2 * lane);
+                        double2 vb =
+                            *reinterpret_cast<const double2*>(S + c * SD_R + 64 + 2 * lane);
+                        va.x = ra < n ? va.x : 0.0;
+                        va.y = ra + 1 < n ? va.y : 0.0;
+                        vb.x = rb < n ? vb.x : 0.0;
+                        vb.y = rb + 1 < n ? vb.y : 0.0;
+                        acc[k] = fma(va.x, wa.x, acc[k]);
+                        acc[k] = fma(va.y, wa.y, acc[k]);
+                        acc[k] = fma(vb.x, wb.x, acc[k]);
+                        acc[k] = fma(vb.y, wb.y, acc[k]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // stage st is free again
+        if (tid == 0 && t + 2 * step < ntiles) {
+            // order this CTA's reads of the stage before the bulk copy that
+            // overwrites it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(t + 2 * step, st);
+        }
+    }
+    if (!ok) {
+        // the copies did not arrive: flag it, give the copies this CTA issued
+        // a bounded chance to land, and leave without touching the results
+        if (tid == 0) {
+            atomicExch(err, 1u);
+            for (int j = 0; j < 2; ++j) {
+                const int kk = k_local + j;   // outstanding tiles k_local, k_local + 1
+                if (first + kk * step < ntiles)
+                    mbar_wait_bounded(smem_u32(&bar[kk & 1]), (uint32_t)((kk >> 1) & 1));
+            }
+        }
+        return;
+    }
+    // per-CTA partial sums of each column over this CTA's rows
+#pragma unroll
+    for (int k = 0; k < SD_CPW; ++k) {
+        const int c = warp + k * ORTHO_WARPS;
+        if (c < ncol) {
+            const double v = warp_sum(acc[k]);
+            if (lane == 0) part[(size_t)blockIdx.x * PART_STRIDE + c] = v;
+        }
+    }
+    if (last_block_done(counter)) {
+        __threadfence();
+        final_reduce(part, gridDim.x, ncol, hout);
+        if (tid == 0) *counter = 0u;
+    }
+}
+
 // CTAs of a kernel resident at once on the current device (occupancy x
 // SMs), cached per device and kernel slot
 template <typename K>
@@ -334,6 +559,59 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_gemv_sub"); return PPG_ERR_CUDA; }
     return check_launch("k_gemv_sub");
+}
+
+// the fused pass applies when V's columns and w are 16-byte aligned and
+// padded to ldv rows (a multiple of 64: every tile copy is whole 16-byte
+// granules), w is a column of the same padded basis, and ncol <= SD_MAXC
+bool cgs_fused_ok(const double* V, int64_t ldv, int ncol, const double* w) {
+    return ncol >= 1 && ncol <= SD_MAXC && (ldv % 64) == 0 &&
+           (((uintptr_t)V | (uintptr_t)w) & 15) == 0;
+}
+
+static size_t sub_dot_smem(int ncol) { return (size_t)2 * (ncol + 1) * SD_R * sizeof(double); }
+
+// resident CTAs of k_sub_dot for a column count (dynamic shared memory
+// depends on it), cached per device
+static int sub_dot_resident(int ncol) {
+    static std::atomic<int> cached[16][SD_MAXC + 1];
+    static std::atomic<int> attr_set[16];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
+    if (!attr_set[dev].load(std::memory_order_relaxed)) {
+        cudaFuncSetAttribute(k_sub_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sub_dot_smem(SD_MAXC));
+        attr_set[dev].store(1, std::memory_order_relaxed);
+    }
+    int v = cached[dev][ncol].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sub_dot, ORTHO_THREADS,
+                                                          sub_dot_smem(ncol)) != cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        v = occ * device_sm_count();
+        cached[dev][ncol].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+int32_t launch_cgs_sub_dot(const double* V, int64_t ldv, int ncol, double* w, int32_t n,
+                           const double* h1, double* h2_out, const OrthoWs& ws,
+                           cudaStream_t s) {
+    if (!cgs_fused_ok(V, ldv, ncol, w) || n < 1 || ldv < n) return PPG_ERR_ARG;
+    const int ntiles = (int)(((int64_t)n + SD_R - 1) / SD_R);
+    // one wave of resident CTAs, at most the grid_cap(8) row blocks the
+    // partial-sum buffer holds
+    const int grid = max(1, min(min(sub_dot_resident(ncol), ntiles), grid_cap(8)));
+    const cudaError_t e = launch_pdl(k_sub_dot, dim3(grid), dim3(ORTHO_THREADS),
+                                     sub_dot_smem(ncol), s, V, ldv, ncol, w, n, h1, ws.part,
+                                     ws.counter + 2, h2_out, ws.counter + 3);
+    ++g_launches;
+    if (e != cudaSuccess) { set_cuda_error(e, "launch k_sub_dot"); return PPG_ERR_CUDA; }
+    return check_launch("k_sub_dot");
 }
 
 // ---------------------------------------------------------------------------

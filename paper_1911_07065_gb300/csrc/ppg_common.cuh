@@ -204,7 +204,9 @@ int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr,
 
 struct OrthoWs {
     double* part;       // [ortho_part_doubles(grid)]
-    unsigned* counter;  // [4] zero-initialised, self-resetting
+    unsigned* counter;  // [4] zero-initialised: [0..2] self-resetting CTA
+                        // counters of the passes, [3] error flag (a staging
+                        // wait of the fused pass gave up)
     double* h1;         // [MAXC + 2]
     double* h2;         // [MAXC + 2]
     double* nrm;        // [4]
@@ -224,6 +226,15 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w,
 int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w,
                           int32_t n, const double* hin, bool with_norm, double* nrm_out,
                           const OrthoWs& ws, cudaStream_t s);
+
+// w -= V h1 and h2_out = V^T w (the updated w) in one pass: CGS2 passes 2
+// and 3 fused.  Needs cgs_fused_ok(V, ldv, ncol, w): V and w 16-byte
+// aligned, ldv a multiple of 64, w a column of the same padded basis (ldv
+// rows readable), ncol <= 56.
+bool cgs_fused_ok(const double* V, int64_t ldv, int ncol, const double* w);
+int32_t launch_cgs_sub_dot(const double* V, int64_t ldv, int ncol, double* w, int32_t n,
+                           const double* h1, double* h2_out, const OrthoWs& ws,
+                           cudaStream_t s);
 
 struct GmresState {   // device, one per solve
     double* R;        // (m+1) x m column-major, rotated Hessenberg
