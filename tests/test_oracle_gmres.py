@@ -120,6 +120,124 @@ def test_fgmres_fp32_inner_reaches_fp64_accuracy():
     assert 1e-9 < rel < 1e-3
 
 
+def _alg3_coef64(A, coef, v):
+    """Algorithm 3 in FP64 arithmetic on given coefficients (the float32
+    ones, widened): with the float32 matrix and vector it isolates the
+    effect of rounding the DATA to float32 from that of float32 ARITHMETIC."""
+    d = len(coef)
+    prod = v.copy()
+    p = np.zeros_like(v)
+    i = 0
+    while i < d - 1:
+        kind, c1, c2 = coef[i]
+        c1, c2 = float(c1), float(c2)
+        if kind == "r":
+            p = p + c1 * prod
+            prod = prod - c1 * (A @ prod)
+            i += 1
+        else:
+            tmp = c1 * prod - A @ prod
+            p = p + c2 * tmp
+            if i <= d - 3:
+                prod = prod - c2 * (A @ tmp)
+            i += 2
+    if coef[d - 1][0] == "r" and i == d - 1:
+        p = p + float(coef[d - 1][1]) * prod
+    return p
+
+
+def _alg3_magnitudes(Aabs, coef, vabs):
+    """The same recurrence on magnitudes: |A|, |coefficients|, |v|, every
+    subtraction an addition.  Each intermediate of a float32 evaluation is
+    bounded in magnitude by the matching quantity here."""
+    d = len(coef)
+    prod = vabs.copy()
+    p = np.zeros_like(vabs)
+    i = 0
+    while i < d - 1:
+        kind, c1, c2 = coef[i]
+        c1, c2 = abs(float(c1)), abs(float(c2))
+        if kind == "r":
+            p = p + c1 * prod
+            prod = prod + c1 * (Aabs @ prod)
+            i += 1
+        else:
+            tmp = c1 * prod + Aabs @ prod
+            p = p + c2 * tmp
+            if i <= d - 3:
+                prod = prod + c2 * (Aabs @ tmp)
+            i += 2
+    if coef[d - 1][0] == "r" and i == d - 1:
+        p = p + abs(float(coef[d - 1][1])) * prod
+    return p
+
+
+def _slip(coef, k, rel):
+    """coef with entry k's coefficient scaled by (1 + rel) (a planted mistake)."""
+    coef = list(coef)
+    kind, c1, c2 = coef[k]
+    coef[k] = (kind, np.float32(float(c1) * (1 + rel)), c2) if kind == "r" else \
+        (kind, c1, np.float32(float(c2) * (1 + rel)))
+    return coef
+
+
+def test_apply_p32_short_chains_within_the_rounding_bound():
+    """Rigorous first-order bound (running error analysis) on chains of one
+    to three roots, where it is tight: with the float32 data fixed, every
+    rounded float32 operation adds at most u |result| (u = 2^-24) and along
+    any path there are at most N = steps x (longest row + 3) roundings, so
+    |z32 - z| <= gamma_N S elementwise, S from the magnitude recurrence and
+    z the same data in FP64 arithmetic.  A coefficient 1e-4 off breaks it."""
+    P = synth.problem("cd3d_160", scale=10)
+    As = P.A.to_scipy()
+    A32 = As.astype(np.float32)
+    A32d = A32.astype(np.float64)
+    v32 = P.b.astype(np.float32)
+    u = 2.0 ** -24
+    kmax = int(np.diff(As.indptr).max())
+    for roots in (np.array([4.0, 6.5], dtype=complex),
+                  np.array([5 + 1j, 5 - 1j, 3.0]),
+                  np.array([5 + 1j, 5 - 1j]),
+                  np.array([2.5, 5 + 1j, 5 - 1j, 3.0])):
+        coef = gmres._roots32(roots)
+        z32 = gmres.apply_p32(A32, coef, v32).astype(np.float64)
+        z = _alg3_coef64(A32d, coef, v32.astype(np.float64))
+        N = len(roots) * (kmax + 3) + 1
+        bound = N * u / (1 - N * u) * _alg3_magnitudes(abs(A32d), coef, np.abs(v32))
+        err = np.abs(z32 - z)
+        assert np.all(err <= bound), float(np.max(err / bound))
+        assert np.max(err) > 0.0
+        bad = gmres.apply_p32(A32, _slip(coef, 0, 1e-4), v32).astype(np.float64)
+        assert np.any(np.abs(bad - z) > bound)
+
+
+def test_apply_p32_arithmetic_error_comparable_to_data_rounding():
+    """Whole chains (degrees 6 to 30): the float32 ARITHMETIC of the oracle's
+    Algorithm 3 adds an error within 10x of the error that rounding the data
+    alone (matrix, coefficients, v) to float32 causes, and within 1e-6 of
+    ||p(A) v|| -- so a float32 path less accurate than its data rounding
+    warrants fails here (a coefficient 1e-3 off does)."""
+    P = synth.problem("cd3d_160", scale=12)
+    As = P.A.to_scipy()
+    A32 = As.astype(np.float32)
+    A32d = A32.astype(np.float64)
+    v = P.b
+    v32d = v.astype(np.float32).astype(np.float64)
+    for deg, stab in ((6, True), (12, True), (20, False), (30, True)):
+        roots = poly.build_poly(As, deg, P.v0, stability=stab).roots
+        coef = gmres._roots32(roots)
+        z64 = poly.apply_p(As, roots, v)
+        zd = _alg3_coef64(A32d, coef, v32d)
+        z32 = gmres.apply_p32(A32, coef, v).astype(np.float64)
+        e_arith = np.linalg.norm(z32 - zd)
+        e_data = np.linalg.norm(zd - z64)
+        nz = np.linalg.norm(z64)
+        assert 0.0 < e_arith <= 10.0 * e_data, (deg, e_arith / e_data)
+        assert np.linalg.norm(z32 - z64) <= 1e-6 * nz
+        bad = gmres.apply_p32(A32, _slip(coef, 0, 1e-3), v).astype(np.float64)
+        assert np.linalg.norm(bad - zd) > 10.0 * e_data
+
+
 def test_stability_check_small_for_stable_and_large_for_unstable():
     """Section 3.5: StCh is at rounding level for a tame polynomial and
     large for a high-degree one without root adding on a matrix with an
