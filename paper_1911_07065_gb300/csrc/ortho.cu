@@ -272,27 +272,30 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
 // ---------------------------------------------------------------------------
 // CGS2 passes 2 and 3 in one pass over V:  w -= V h1, then h2 = V^T w of the
 // updated w.  The update of a row needs only that row of V, so a tile of
-// rows is staged in shared memory once and serves both products: 3/4 of the
-// unfused passes' bytes, the same FP64 multiply-adds.
+// rows is read from HBM once and serves both products: 3/4 of the unfused
+// passes' bytes, the same FP64 multiply-adds.
 //
-// Tiles of SD_R rows x ncol columns (plus the tile of w) move from HBM to
-// shared memory with one bulk copy per column (the TMA engine; column c of
-// the tile is one contiguous 1 KB range of the column-major basis), double
-// buffered on two mbarriers, so the threads issue no load instructions for
-// V at all.  Phase 1: thread (row pair p, column group q) sums V[r, c] h1[c]
-// over its quarter of the columns; the four partial sums of a row are added
-// in a fixed order and w' = w - s is written back.  Phase 2: warp k owns
-// columns k, k + 8, ... (at most SD_MAXC / 8 per warp) and each lane adds
-// V[r, c] w'[r] for four rows of the tile into per-column accumulators that
-// persist across the CTA's tiles.  Per-CTA partial sums are reduced by the
-// last CTA in a fixed order (deterministic).
+// Tiles of SD_R rows x ncol columns move from HBM to shared memory with one
+// bulk copy per column (the TMA engine; column c of the tile is one
+// contiguous 1 KB range of the column-major basis), double buffered on two
+// mbarriers.  Each thread then takes a register block of the tile -- warp k
+// owns a contiguous run of at most SD_CPW columns, lane l the rows 2l, 2l+1,
+// 64+2l, 65+2l -- with one 16-byte shared load per two elements, and uses
+// it twice: phase 1 sums V[r, c] h1[c] over the warp's columns into
+// per-warp row partials, which are added in warp order to give
+// w' = w - V h1; phase 2 adds V[r, c] w'[r] into per-column accumulators
+// that persist across the CTA's tiles.  So every element costs two FP64
+// multiply-adds and half a shared load: on GB300, where the FP64 pipe
+// issues at half the instruction rate, the multiply-adds set the pace.
+// Per-CTA partial sums are reduced by the last CTA in a fixed order
+// (deterministic).
 //
 // Every wait on an mbarrier is bounded; a CTA whose copies do not arrive
 // sets *err, waits (bounded) for the copies it issued, and returns.
 // ---------------------------------------------------------------------------
 
 constexpr int SD_R = 128;                 // rows per tile
-constexpr int SD_MAXC = 56;               // columns (7 per warp)
+constexpr int SD_MAXC = 56;               // columns (at most 7 per warp)
 constexpr int SD_CPW = SD_MAXC / ORTHO_WARPS;
 constexpr uint32_t SD_SPIN_LIMIT = 1u << 22;
 
@@ -319,18 +322,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__global__ void __launch_bounds__(ORTHO_THREADS)
+__global__ void __launch_bounds__(ORTHO_THREADS, 2)
 k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
           const double* __restrict__ h1, double* part, unsigned* counter, double* hout,
           unsigned* err) {
-    extern __shared__ __align__(128) double sd_stage[];   // 2 x (ncol + 1) x SD_R
-    __shared__ double sh[SD_MAXC];
-    __shared__ __align__(16) double spart[4][SD_R];
+    extern __shared__ __align__(128) double sd_stage[];   // 2 x ncol x SD_R
+    __shared__ __align__(16) double spart[ORTHO_WARPS][SD_R];
     __shared__ __align__(16) double ws[SD_R];
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t stage_elems = (int64_t)(ncol + 1) * SD_R;   // w's tile is slot ncol
+    const int64_t stage_elems = (int64_t)ncol * SD_R;
     const int ntiles = (int)(((int64_t)n + SD_R - 1) / SD_R);
+    // this warp's columns [c0, c0 + nc), near-equal runs
+    const int c0 = warp * ncol / ORTHO_WARPS;
+    const int nc = (warp + 1) * ncol / ORTHO_WARPS - c0;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
@@ -338,7 +343,9 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
     }
     PPG_PDL_TRIGGER();
     PPG_PDL_WAIT();   // h1 and w come from the kernels before this one
-    for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = h1[c];
+    double hreg[SD_CPW];
+#pragma unroll
+    for (int k = 0; k < SD_CPW; ++k) hreg[k] = k < nc ? h1[c0 + k] : 0.0;
     __syncthreads();
 
     // thread 0: tile t into stage st (rows up to the padded column length,
@@ -350,13 +357,12 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
         const uint32_t b = smem_u32(&bar[st]);
         double* dst = sd_stage + st * stage_elems;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                     "r"(bytes * (uint32_t)(ncol + 1))
+                     "r"(bytes * (uint32_t)ncol)
                      : "memory");
-        for (int c = 0; c <= ncol; ++c) {
-            const double* src = (c < ncol ? V + c * ldv : w) + r0;
+        for (int c = 0; c < ncol; ++c) {
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                ::"r"(smem_u32(dst + c * SD_R)), "l"(src), "r"(bytes), "r"(b)
+                ::"r"(smem_u32(dst + c * SD_R)), "l"(V + c * ldv + r0), "r"(bytes), "r"(b)
                 : "memory");
         }
     };
@@ -370,99 +376,99 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
     double acc[SD_CPW];
 #pragma unroll
     for (int k = 0; k < SD_CPW; ++k) acc[k] = 0.0;
-    const int p = tid & 63, q = tid >> 6;   // phase 1: row pair, column group
     int k_local = 0;
     bool ok = true;
     for (int t = first; t < ntiles; t += step, ++k_local) {
         const int st = k_local & 1;
-        const uint32_t parity = (uint32_t)((k_local >> 1) & 1);
-        const bool mine = mbar_wait_bounded(smem_u32(&bar[st]), parity);
+        const int64_t r0 = (int64_t)t * SD_R;
+        // the combining threads fetch their two rows of w early
+        double2 wv = make_double2(0.0, 0.0);
+        const int64_t gw = r0 + 2 * tid;
+        if (tid < SD_R / 2) {
+            if (gw + 1 < n) {
+                wv = *reinterpret_cast<const double2*>(w + gw);
+            } else if (gw < n) {
+                wv.x = w[gw];
+            }
+        }
+        const bool mine = mbar_wait_bounded(smem_u32(&bar[st]), (uint32_t)((k_local >> 1) & 1));
         if (!__syncthreads_and(mine)) {
             ok = false;
             break;
         }
         const double* S = sd_stage + st * stage_elems;
-        const int64_t r0 = (int64_t)t * SD_R;
-        // phase 1: partial sums of (V h1)[r] over columns q, q + 4, ...
-        {
-            double s0 = 0.0, s1 = 0.0;
-            for (int c = q; c < ncol; c += 4) {
-                const double2 v = *reinterpret_cast<const double2*>(S + c * SD_R + 2 * p);
-                const double hc = sh[c];
-                s0 = fma(v.x, hc, s0);
-                s1 = fma(v.y, hc, s1);
-            }
-            spart[q][2 * p] = s0;
-            spart[q][2 * p + 1] = s1;
-        }
-        __syncthreads();
-        if (tid < 64) {
-            const int r = 2 * tid;
-            const double2 wv = *reinterpret_cast<const double2*>(S + ncol * SD_R + r);
-            const double sa = ((spart[0][r] + spart[1][r]) + spart[2][r]) + spart[3][r];
-            const double sb =
-                ((spart[0][r + 1] + spart[1][r + 1]) + spart[2][r + 1]) + spart[3][r + 1];
-            const int64_t g = r0 + r;
-            double2 o;
-            o.x = g < n ? wv.x - sa : 0.0;
-            o.y = g + 1 < n ? wv.y - sb : 0.0;
-            *reinterpret_cast<double2*>(ws + r) = o;
-            if (g + 1 < n) {
-                *reinterpret_cast<double2*>(w + g) = o;
-            } else if (g < n) {
-                w[g] = o.x;
-            }
-        }
-        __syncthreads();
-        // phase 2: this warp's columns against the tile's w' (rows 2 lane,
-        // 2 lane + 1, 64 + 2 lane, 65 + 2 lane).  Rows at or past n hold the
-        // basis's padding (never written, possibly not finite): in the last,
-        // partial tile they are replaced by zeros before the multiply-adds.
-        {
-            const double2 wa = *reinterpret_cast<const double2*>(ws + 2 * lane);
-            const double2 wb = *reinterpret_cast<const double2*>(ws + 64 + 2 * lane);
-            if (r0 + SD_R <= n) {
+        // this thread's register block; rows at or past n hold the basis's
+        // padding (never written, possibly not finite) and become zeros
+        double2 va[SD_CPW], vb[SD_CPW];
+        const bool full = r0 + SD_R <= n;
+        const int64_t ra = r0 + 2 * lane, rb = r0 + 64 + 2 * lane;
 #pragma unroll
-                for (int k = 0; k < SD_CPW; ++k) {
-                    const int c = warp + k * ORTHO_WARPS;
-                    if (c < ncol) {   // uniform over the warp: no FMA for a missing column
-                        const double2 va =
-                            *reinterpret_cast<const double2*>(S + c * SD_R + 2 * lane);
-                        const double2 vb =
-                            *reinterpret_cast<const double2*>(S + c * SD_R + 64 + 2 * lane);
-                        acc[k] = fma(va.x, wa.x, acc[k]);
-                        acc[k] = fma(va.y, wa.y, acc[k]);
-                        acc[k] = fma(vb.x, wb.x, acc[k]);
-                        acc[k] = fma(vb.y, wb.y, acc[k]);
-                    }
-                }
-            } else {
-                const int64_t ra = r0 + 2 * lane, rb = r0 + 64 + 2 * lane;
-#pragma unroll
-                for (int k = 0; k < SD_CPW; ++k) {
-                    const int c = warp + k * ORTHO_WARPS;
-                    if (c < ncol) {
-                        double2 va = *reinterpret_cast<const double2*>(S + c * SD_R + 2 * lane);
-                        double2 vb =
-                            *reinterpret_cast<const double2*>(S + c * SD_R + 64 + 2 * lane);
-                        va.x = ra < n ? va.x : 0.0;
-                        va.y = ra + 1 < n ? va.y : 0.0;
-                        vb.x = rb < n ? vb.x : 0.0;
-                        vb.y = rb + 1 < n ? vb.y : 0.0;
-                        acc[k] = fma(va.x, wa.x, acc[k]);
-                        acc[k] = fma(va.y, wa.y, acc[k]);
-                        acc[k] = fma(vb.x, wb.x, acc[k]);
-                        acc[k] = fma(vb.y, wb.y, acc[k]);
-                    }
+        for (int k = 0; k < SD_CPW; ++k) {
+            if (k < nc) {   // uniform over the warp: no FMA for a missing column
+                va[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 2 * lane);
+                vb[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 64 + 2 * lane);
+                if (!full) {
+                    va[k].x = ra < n ? va[k].x : 0.0;
+                    va[k].y = ra + 1 < n ? va[k].y : 0.0;
+                    vb[k].x = rb < n ? vb[k].x : 0.0;
+                    vb[k].y = rb + 1 < n ? vb[k].y : 0.0;
                 }
             }
         }
-        __syncthreads();   // stage st is free again
+        // phase 1: row partials of V h1 over this warp's columns
+        {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll
+            for (int k = 0; k < SD_CPW; ++k) {
+                if (k < nc) {
+                    s0 = fma(va[k].x, hreg[k], s0);
+                    s1 = fma(va[k].y, hreg[k], s1);
+                    s2 = fma(vb[k].x, hreg[k], s2);
+                    s3 = fma(vb[k].y, hreg[k], s3);
+                }
+            }
+            *reinterpret_cast<double2*>(&spart[warp][2 * lane]) = make_double2(s0, s1);
+            *reinterpret_cast<double2*>(&spart[warp][64 + 2 * lane]) = make_double2(s2, s3);
+        }
+        __syncthreads();   // the stage is in registers; the partials are complete
         if (tid == 0 && t + 2 * step < ntiles) {
             // order this CTA's reads of the stage before the bulk copy that
             // overwrites it
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(t + 2 * step, st);
+        }
+        if (tid < SD_R / 2) {
+            const int r = 2 * tid;
+            double sa = 0.0, sb = 0.0;
+#pragma unroll
+            for (int g = 0; g < ORTHO_WARPS; ++g) {
+                sa += spart[g][r];
+                sb += spart[g][r + 1];
+            }
+            double2 o;
+            o.x = gw < n ? wv.x - sa : 0.0;
+            o.y = gw + 1 < n ? wv.y - sb : 0.0;
+            *reinterpret_cast<double2*>(ws + r) = o;
+            if (gw + 1 < n) {
+                *reinterpret_cast<double2*>(w + gw) = o;
+            } else if (gw < n) {
+                w[gw] = o.x;
+            }
+        }
+        __syncthreads();
+        // phase 2: column partials of V^T w' over this lane's four rows
+        {
+            const double2 wa = *reinterpret_cast<const double2*>(ws + 2 * lane);
+            const double2 wb = *reinterpret_cast<const double2*>(ws + 64 + 2 * lane);
+#pragma unroll
+            for (int k = 0; k < SD_CPW; ++k) {
+                if (k < nc) {
+                    acc[k] = fma(va[k].x, wa.x, acc[k]);
+                    acc[k] = fma(va[k].y, wa.y, acc[k]);
+                    acc[k] = fma(vb[k].x, wb.x, acc[k]);
+                    acc[k] = fma(vb[k].y, wb.y, acc[k]);
+                }
+            }
         }
     }
     if (!ok) {
@@ -481,10 +487,9 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
     // per-CTA partial sums of each column over this CTA's rows
 #pragma unroll
     for (int k = 0; k < SD_CPW; ++k) {
-        const int c = warp + k * ORTHO_WARPS;
-        if (c < ncol) {
+        if (k < nc) {
             const double v = warp_sum(acc[k]);
-            if (lane == 0) part[(size_t)blockIdx.x * PART_STRIDE + c] = v;
+            if (lane == 0) part[(size_t)blockIdx.x * PART_STRIDE + c0 + k] = v;
         }
     }
     if (last_block_done(counter)) {
@@ -569,7 +574,7 @@ bool cgs_fused_ok(const double* V, int64_t ldv, int ncol, const double* w) {
            (((uintptr_t)V | (uintptr_t)w) & 15) == 0;
 }
 
-static size_t sub_dot_smem(int ncol) { return (size_t)2 * (ncol + 1) * SD_R * sizeof(double); }
+static size_t sub_dot_smem(int ncol) { return (size_t)2 * ncol * SD_R * sizeof(double); }
 
 // resident CTAs of k_sub_dot for a column count (dynamic shared memory
 // depends on it), cached per device
