@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define PPG_ABI_VERSION 1
+#define PPG_ABI_VERSION 2
 
 /* status codes */
 #define PPG_OK                0
@@ -94,6 +94,14 @@ typedef struct ppg_opts {
     double  pof_step_log10;        /* default 14 (one more per factor 1e14) */
     int32_t timing;                /* 1: record CUDA-event times into stats */
     int32_t x0_given;              /* 1: x holds the initial guess (default 0: x0 = 0) */
+    int32_t batch_mode;            /* ppg_solve_batched: 0 = every restart cycle of every
+                                      solve in one persistent cooperative launch (default),
+                                      1 = one CUDA graph per restart cycle, replayed by a
+                                      host loop */
+    int32_t pad_;
+    double  wait_timeout_ms;       /* limit of each grid-wide barrier wait of the persistent
+                                      launch (default 5000); a wait that runs out ends the
+                                      launch with PPG_ERR_TIMEOUT */
 } ppg_opts;
 
 typedef struct ppg_stats {
@@ -277,9 +285,16 @@ int32_t ppg_solve_chpoly(const ppg_csr* A, int32_t d, const double* b, double* x
  * FP64 with z = p(A_s) v applied by Algorithm 3 in FP32 (the precision
  * form of ppg_solve_flex).  All systems and right-hand sides advance in the
  * same launches: the systems are packed block-diagonally (each padded to
- * 256-row tiles), the right-hand sides interleaved, and a restart cycle of
- * the whole batch is replayed as one CUDA graph (captured on `stream`;
- * on the legacy default stream the cycle is launched directly).
+ * 256-row tiles) and the right-hand sides interleaved.  With
+ * opts->batch_mode = 0 (default) every restart cycle of every solve runs
+ * in ONE persistent cooperative kernel launch (captured as a one-node CUDA
+ * graph on `stream`, launched directly on the legacy default stream), its
+ * phases separated by grid-wide barriers whose waits are bounded by
+ * opts->wait_timeout_ms (PPG_ERR_TIMEOUT when one runs out); with
+ * batch_mode = 1 a restart cycle of the whole batch is captured as a CUDA
+ * graph of many kernels and replayed once per cycle from a host loop.  The
+ * rows per group of the FP32 root step (64, 128 or 256) are chosen by
+ * timing the candidates on the batch (cached per batch shape).
  *   As      host array of nsys CSR descriptors (PPG_F64, device pointers)
  *   B, X    host arrays of nsys device pointers, each n_s * nrhs doubles,
  *           column-major (right-hand side k at offset k * n_s)

@@ -42,7 +42,8 @@ class ppg_roots(C.Structure):
 class ppg_opts(C.Structure):
     _fields_ = [("max_cycles", c_i32), ("stability_control", c_i32),
                 ("pof_threshold_log10", c_f64), ("pof_step_log10", c_f64),
-                ("timing", c_i32), ("x0_given", c_i32)]
+                ("timing", c_i32), ("x0_given", c_i32), ("batch_mode", c_i32),
+                ("pad_", c_i32), ("wait_timeout_ms", c_f64)]
 
 
 class ppg_stats(C.Structure):

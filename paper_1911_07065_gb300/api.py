@@ -246,12 +246,14 @@ def solve_chpoly(A: CSR, b: torch.Tensor, d: int, m: int = 50, tol: float = 1e-1
 
 
 def solve_batched(As, Bs, v0s, d: int = 20, m: int = 30, tol: float = 1e-10,
-                  max_cycles: int = 10000, Xs=None, stream=None):
+                  max_cycles: int = 10000, Xs=None, stream=None, persistent: bool = True,
+                  wait_timeout_ms: Optional[float] = None):
     """Batching form: systems As[s] (FP64 CSR) with right-hand sides Bs[s]
     (tensor (nrhs, n_s), nrhs = 1 or 4, same nrhs for all) and start vectors
     v0s[s]; each system gets its own polynomial; FGMRES(m) with FP32 p(A).
-    Returns (Xs, info) with info = {"roots", "relres", "iters", "stats",
-    "status"}."""
+    persistent: the whole solve in one persistent cooperative launch (else
+    one CUDA graph per restart cycle).  Returns (Xs, info) with info =
+    {"roots", "relres", "iters", "stats", "status"}."""
     nsys = len(As)
     nrhs = Bs[0].shape[0] if Bs[0].dim() == 2 else 1
     csrs = (ppg_csr * nsys)(*[A.s for A in As])
@@ -266,7 +268,8 @@ def solve_batched(As, Bs, v0s, d: int = 20, m: int = 30, tol: float = 1e-10,
     rarr = (ppg_roots * nsys)(*[r.s for r in roots])
     rel = np.zeros(nsys * nrhs)
     its = np.zeros(nsys * nrhs, dtype=np.int32)
-    o = default_opts(max_cycles=max_cycles)
+    o = default_opts(max_cycles=max_cycles, batch_mode=0 if persistent else 1,
+                     wait_timeout_ms=wait_timeout_ms)
     st = ppg_stats()
     rc = lib.ppg_solve_batched(nsys, csrs, nrhs, bp, xp, vp, d, m, tol, C.byref(o), rarr,
                                C.byref(st), _dp(rel),

@@ -1020,6 +1020,9 @@ void ppg_default_opts(ppg_opts* o) {
     o->pof_step_log10 = 14.0;
     o->timing = 0;
     o->x0_given = 0;
+    o->batch_mode = 0;
+    o->pad_ = 0;
+    o->wait_timeout_ms = 5000.0;
 }
 
 int32_t ppg_harmonic_ritz(const double* Hbar, int32_t ldh, int32_t d, double* re, double* im) {

@@ -87,33 +87,38 @@ __device__ __forceinline__ bool sys_live(const int32_t* active, int s) {
     return any != 0;
 }
 
-// One pass of the batch: step steps[s] of every system s, applied to the
-// NR right-hand sides (one thread per row).  Ops as in the single-system
-// kernel; OP_NOP leaves everything untouched.  OP_RESID writes per-CTA
-// partial sums of squares, part[cta * NR + k].
-// Register bound: 32 per thread (8 CTAs of 256 threads per SM) for the FP32
-// steps and the one-rhs FP64 step, measured 3 % faster on the batching
-// workload than the 40 registers the FP32 step takes unbounded; the FP64
-// four-rhs step would spill at 32.
+// Synchronise the `rows` threads of one row group: the whole CTA when the
+// group is the CTA, else a named barrier of the group (ids 1..4; barrier 0
+// is __syncthreads).
+__device__ __forceinline__ void group_sync(int group, int rows) {
+    if (rows == (int)blockDim.x) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(rows) : "memory");
+    }
+}
+
+// One tile of one pass of the batch: step steps[s] of system s (the owner of
+// the tile) applied to the NR right-hand sides of `rows` consecutive rows,
+// one thread (gt) per row.  Ops as in the single-system kernel; OP_NOP
+// leaves everything untouched.  OP_RESID writes the tile's partial sums of
+// squares, part[vt * NR + k] (only with rows == blockDim.x).  The staging
+// buffers sval / scol hold `chunk` nonzeros, srp rows + 1 row pointers.
 template <typename T, int NR>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 || NR == 1) ? 8 : 4)
-k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-        const T* __restrict__ vals, const BStep* __restrict__ steps,
-        const int32_t* __restrict__ sys_of_tile, BufSet<T> b, double* part,
-        const int32_t* __restrict__ active) {
-    __shared__ T sval[BCHUNK];
-    __shared__ int32_t scol[BCHUNK];
-    __shared__ int32_t srp[BT + 1];
-    __shared__ double sred[8][NR];
-    const int tid = threadIdx.x;
-    const int rows = blockDim.x;
-    const int64_t row0 = (int64_t)blockIdx.x * rows;
+__device__ __forceinline__ void bstep_tile(
+    int64_t vt, int rows, int gt, int group, T* sval, int32_t* scol, int32_t* srp, int chunk,
+    double (*sred)[NR], const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+    const T* __restrict__ vals, const BStep* __restrict__ steps,
+    const int32_t* __restrict__ sys_of_tile, const BufSet<T>& b, double* part,
+    const int32_t* __restrict__ active) {
+    const int tid = gt;
+    const int64_t row0 = vt * rows;
     const int s = sys_of_tile[row0 / BT];
     const BStep st = steps[s];
-    if (st.op == OP_NOP) return;   // uniform over the CTA
+    if (st.op == OP_NOP) return;   // uniform over the group
     if (active && !sys_live<NR>(active, s)) return;   // every solve of s has stopped
     for (int i = tid; i <= rows; i += rows) srp[i] = __ldg(rowptr + row0 + i);
-    __syncthreads();
+    group_sync(group, rows);
     const int32_t k0 = srp[0], k1 = srp[rows];
     const int32_t lo_r = srp[tid], hi_r = srp[tid + 1];
     const int64_t r = row0 + tid;
@@ -130,8 +135,8 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
     T acc[NR];
 #pragma unroll
     for (int i = 0; i < NR; ++i) acc[i] = T(0);
-    for (int32_t c0 = k0; c0 < k1; c0 += BCHUNK) {
-        const int32_t c1 = min(k1, c0 + BCHUNK);
+    for (int32_t c0 = k0; c0 < k1; c0 += chunk) {
+        const int32_t c1 = min(k1, c0 + chunk);
         // asynchronous, coalesced staging of the tile's values and columns
         for (int32_t k = c0 + tid; k < c1; k += rows) {
             const unsigned sv_ = (unsigned)__cvta_generic_to_shared(sval + (k - c0));
@@ -142,7 +147,7 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                          : "memory");
         }
         asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
+        group_sync(group, rows);
         const int32_t lo = max(lo_r, c0) - c0, hi = min(hi_r, c1) - c0;
         int32_t k = lo;
         // one FMA per nonzero and right-hand side, the gathers of two
@@ -162,7 +167,7 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
 #pragma unroll
             for (int i = 0; i < NR; ++i) acc[i] = fma(v0, x0[i], acc[i]);
         }
-        __syncthreads();
+        group_sync(group, rows);
     }
     const T c1 = (T)st.c1, c2 = (T)st.c2, c3 = (T)st.c3;
     T* o0 = st.o0 >= 0 ? b.p[st.o0] + r * NR : nullptr;
@@ -212,13 +217,32 @@ k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
             if (lane == 0) sred[warp][i] = v;
         }
-        __syncthreads();
+        group_sync(group, rows);
         if (tid < NR) {
             double t = 0.0;
             for (int w = 0; w < (rows >> 5); ++w) t += sred[w][tid];
-            part[(size_t)blockIdx.x * NR + tid] = t;
+            part[(size_t)vt * NR + tid] = t;
         }
     }
+}
+
+// One pass of the batch over all tiles: one CTA per tile of blockDim.x rows.
+// Register bound: 32 per thread (8 CTAs of 256 threads per SM) for the FP32
+// steps and the one-rhs FP64 step, measured 3 % faster on the batching
+// workload than the 40 registers the FP32 step takes unbounded; the FP64
+// four-rhs step would spill at 32.
+template <typename T, int NR>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 || NR == 1) ? 8 : 4)
+k_bstep(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+        const T* __restrict__ vals, const BStep* __restrict__ steps,
+        const int32_t* __restrict__ sys_of_tile, BufSet<T> b, double* part,
+        const int32_t* __restrict__ active) {
+    __shared__ T sval[BCHUNK];
+    __shared__ int32_t scol[BCHUNK];
+    __shared__ int32_t srp[BT + 1];
+    __shared__ double sred[8][NR];
+    bstep_tile<T, NR>(blockIdx.x, blockDim.x, threadIdx.x, 0, sval, scol, srp, BCHUNK, sred,
+                      rowptr, colind, vals, steps, sys_of_tile, b, part, active);
 }
 
 template <int NR, int NQ>
@@ -241,20 +265,23 @@ __device__ __forceinline__ void bdot_unit(const double* const* col, const double
 // Partial dot products per unit (up to BUNIT consecutive tiles of one
 // system): part[unit * pstr + c * NR + k] = sum over the unit's rows of
 // col_c[r, k] * w[r, k], where col_c is basis column c (c < ncol) or w
-// itself (c == ncol, with_self).  Thread t takes rhs k = t % NR of rows
-// t / NR, t / NR + 256 / NR, ... of every tile of the unit.
+// itself (c == ncol, with_self), for the columns of chunk cy (BCH columns
+// from cy * BCH).  Thread t takes rhs k = t % NR of rows t / NR,
+// t / NR + 256 / NR, ... of every tile of the unit.  256 threads.
 template <int NR>
-__global__ void __launch_bounds__(256)
-k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __restrict__ w,
-       int with_self, double* part, int64_t pstr, const int32_t* __restrict__ unit_tile0,
-       const int32_t* __restrict__ sys_of_unit, const int32_t* __restrict__ active) {
-    __shared__ double sred[8][BCH][NR];
+__device__ __forceinline__ void bdot_block(int unit, int cy, double (*sred)[BCH][NR],
+                                           const double* __restrict__ V, int64_t ldV, int ncol,
+                                           const double* __restrict__ w, int with_self,
+                                           double* part, int64_t pstr,
+                                           const int32_t* __restrict__ unit_tile0,
+                                           const int32_t* __restrict__ sys_of_unit,
+                                           const int32_t* __restrict__ active) {
     // stopped systems: their partial sums are never read
-    if (active && !sys_live<NR>(active, sys_of_unit[blockIdx.x])) return;
+    if (active && !sys_live<NR>(active, sys_of_unit[unit])) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = tid % NR;
-    const int t0 = unit_tile0[blockIdx.x], t1 = unit_tile0[blockIdx.x + 1];
-    const int c0 = blockIdx.y * BCH;
+    const int t0 = unit_tile0[unit], t1 = unit_tile0[unit + 1];
+    const int c0 = cy * BCH;
     const int nvals = ncol + (with_self ? 1 : 0);
     const int nq = min(BCH, nvals - c0);
     const double* col[BCH];
@@ -290,18 +317,29 @@ k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __rest
             double t = 0.0;
 #pragma unroll
             for (int ww = 0; ww < 8; ++ww) t += sred[ww][q][kk];
-            part[(size_t)blockIdx.x * pstr + (c0 + q) * NR + kk] = t;
+            part[(size_t)unit * pstr + (c0 + q) * NR + kk] = t;
         }
     }
 }
 
+template <int NR>
+__global__ void __launch_bounds__(256)
+k_bdot(const double* __restrict__ V, int64_t ldV, int ncol, const double* __restrict__ w,
+       int with_self, double* part, int64_t pstr, const int32_t* __restrict__ unit_tile0,
+       const int32_t* __restrict__ sys_of_unit, const int32_t* __restrict__ active) {
+    __shared__ double sred[8][BCH][NR];
+    bdot_block<NR>(blockIdx.x, blockIdx.y, sred, V, ldV, ncol, w, with_self, part, pstr,
+                   unit_tile0, sys_of_unit, active);
+}
+
 // out[c * nsolve + s * NR + k] = sum over units u of system s (in order) of
-// part[u * pstr + c * NR + k], for c < nvals.  One warp per (s, c).
-__global__ void k_bsegsum(const double* part, int64_t pstr, int nvals, int NR,
-                          const int32_t* unit0, int nsys, double* out) {
+// part[u * pstr + c * NR + k], for c < nvals.  One warp per (s, c): the
+// block (s, cy) takes c = cy * 8 + warp.
+__device__ __forceinline__ void bsegsum_block(int s, int cy, const double* part, int64_t pstr,
+                                              int nvals, int NR, const int32_t* unit0,
+                                              int nsys, double* out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x;
-    const int c = blockIdx.y * 8 + warp;
+    const int c = cy * 8 + warp;
     if (s >= nsys || c >= nvals) return;
     const int u0 = unit0[s], u1 = unit0[s + 1];
     const int nsolve = nsys * NR;
@@ -313,23 +351,28 @@ __global__ void k_bsegsum(const double* part, int64_t pstr, int nvals, int NR,
     }
 }
 
+__global__ void k_bsegsum(const double* part, int64_t pstr, int nvals, int NR,
+                          const int32_t* unit0, int nsys, double* out) {
+    bsegsum_block(blockIdx.x, blockIdx.y, part, pstr, nvals, NR, unit0, nsys, out);
+}
+
 // w[r, k] -= sum_c V_c[r, k] h[c, solve(r, k)] over the rows of one unit
-// per CTA; with_norm: per-unit partial sums of the new w[r, k]^2 in
-// part[unit * NR + k].
+// per block; with_norm: per-unit partial sums of the new w[r, k]^2 in
+// part[unit * NR + k].  256 threads.
 template <int NR>
-__global__ void __launch_bounds__(256)
-k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
-       const double* __restrict__ h, int nsolve, const int32_t* __restrict__ unit_tile0,
-       const int32_t* __restrict__ sys_of_unit, int with_norm, double* part,
-       const int32_t* __restrict__ active) {
-    __shared__ double sh[ORTHO_MAXC][NR];
-    __shared__ double sred[8][NR];
+__device__ __forceinline__ void bsub_block(int unit, double (*sh)[NR], double (*sred)[NR],
+                                           const double* __restrict__ V, int64_t ldV, int ncol,
+                                           double* w, const double* __restrict__ h, int nsolve,
+                                           const int32_t* __restrict__ unit_tile0,
+                                           const int32_t* __restrict__ sys_of_unit,
+                                           int with_norm, double* part,
+                                           const int32_t* __restrict__ active) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int k = tid % NR;
     constexpr int RP = 256 / NR;
-    const int s = sys_of_unit[blockIdx.x];
+    const int s = sys_of_unit[unit];
     if (active && !sys_live<NR>(active, s)) return;
-    const int t0 = unit_tile0[blockIdx.x], t1 = unit_tile0[blockIdx.x + 1];
+    const int t0 = unit_tile0[unit], t1 = unit_tile0[unit + 1];
     for (int e = tid; e < ncol * NR; e += 256)
         sh[e / NR][e % NR] = h[(size_t)(e / NR) * nsolve + s * NR + e % NR];
     __syncthreads();
@@ -358,8 +401,20 @@ k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
     if (tid < NR) {
         double t = 0.0;
         for (int ww = 0; ww < 8; ++ww) t += sred[ww][tid];
-        part[(size_t)blockIdx.x * NR + tid] = t;
+        part[(size_t)unit * NR + tid] = t;
     }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256)
+k_bsub(const double* __restrict__ V, int64_t ldV, int ncol, double* w,
+       const double* __restrict__ h, int nsolve, const int32_t* __restrict__ unit_tile0,
+       const int32_t* __restrict__ sys_of_unit, int with_norm, double* part,
+       const int32_t* __restrict__ active) {
+    __shared__ double sh[ORTHO_MAXC][NR];
+    __shared__ double sred[8][NR];
+    bsub_block<NR>(blockIdx.x, sh, sred, V, ldV, ncol, w, h, nsolve, unit_tile0, sys_of_unit,
+                   with_norm, part, active);
 }
 
 struct BState {      // device, per solve (nsolve = nsys * NR)
@@ -383,10 +438,9 @@ struct BState {      // device, per solve (nsolve = nsys * NR)
 // (h <= 1e-13 ||A v_j||); solve mode applies the rotations, updates g and
 // stops the solve (for this cycle) when the shortcut residual reaches tol,
 // on breakdown, or at the cycle's last step.
-__global__ void k_bgivens(BState st, int nsolve, int ldh, int m, int j, const double* h1,
-                          const double* h2, const double* nrm, int build, double tol) {
-    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sv >= nsolve) return;
+__device__ __forceinline__ void bgivens_one(int sv, const BState& st, int nsolve, int ldh, int m,
+                                            int j, const double* h1, const double* h2,
+                                            const double* nrm, int build, double tol) {
     if (!st.active[sv]) {
         st.inv[sv] = 0.0;
         return;
@@ -441,24 +495,35 @@ __global__ void k_bgivens(BState st, int nsolve, int ldh, int m, int j, const do
     }
 }
 
-// w[r, k] *= scale[solve(r, k)]
+__global__ void k_bgivens(BState st, int nsolve, int ldh, int m, int j, const double* h1,
+                          const double* h2, const double* nrm, int build, double tol) {
+    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sv < nsolve) bgivens_one(sv, st, nsolve, ldh, m, j, h1, h2, nrm, build, tol);
+}
+
+// w[r, k] *= scale[solve(r, k)] for elements e = e0, e0 + stride, ...
 template <int NR>
-__global__ void k_bscale(double* w, const double* scale, const int32_t* sys_of_tile,
-                         int64_t total) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void bscale_range(double* w, const double* scale,
+                                             const int32_t* sys_of_tile, int64_t total,
+                                             int64_t e0, int64_t stride) {
+    for (int64_t e = e0; e < total; e += stride) {
         const int64_t row = e / NR;
         const int sv = sys_of_tile[row / BT] * NR + (int)(e % NR);
         w[e] *= scale[sv];
     }
 }
 
-__global__ void k_bbacksolve(BState st, int nsolve, int ldh, int m) {
-    // one warp per solve: row i from the bottom up, the lanes sharing the
-    // sum over the solved entries c > i, lane 0 dividing
-    const int sv = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (sv >= nsolve) return;   // uniform over the warp
+template <int NR>
+__global__ void k_bscale(double* w, const double* scale, const int32_t* sys_of_tile,
+                         int64_t total) {
+    bscale_range<NR>(w, scale, sys_of_tile, total, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                     (int64_t)gridDim.x * blockDim.x);
+}
+
+// one warp per solve: row i from the bottom up, the lanes sharing the sum
+// over the solved entries c > i, lane 0 dividing
+__device__ __forceinline__ void bbacksolve_warp(int sv, int lane, const BState& st, int ldh,
+                                                int m) {
     const int k = st.ksteps[sv];
     const double* R = st.R + (size_t)sv * ldh * m;
     const double* g = st.g + (size_t)sv * (m + 1);
@@ -472,12 +537,18 @@ __global__ void k_bbacksolve(BState st, int nsolve, int ldh, int m) {
     }
 }
 
+__global__ void k_bbacksolve(BState st, int nsolve, int ldh, int m) {
+    const int sv = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (sv < nsolve) bbacksolve_warp(sv, threadIdx.x & 31, st, ldh, m);   // uniform per warp
+}
+
 // x[r, k] += sum_{c < ksteps} Z_c[r, k] y[solve][c]
 template <int NR>
-__global__ void k_bzy(const float* __restrict__ Z, int64_t ldZ, double* x, BState st,
-                      const int32_t* __restrict__ sys_of_tile, int m, int64_t total) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void bzy_range(const float* __restrict__ Z, int64_t ldZ, double* x,
+                                          const BState& st,
+                                          const int32_t* __restrict__ sys_of_tile, int m,
+                                          int64_t total, int64_t e0, int64_t stride) {
+    for (int64_t e = e0; e < total; e += stride) {
         const int64_t row = e / NR;
         const int sv = sys_of_tile[row / BT] * NR + (int)(e % NR);
         const int k = st.ksteps[sv];
@@ -488,12 +559,18 @@ __global__ void k_bzy(const float* __restrict__ Z, int64_t ldZ, double* x, BStat
     }
 }
 
+template <int NR>
+__global__ void k_bzy(const float* __restrict__ Z, int64_t ldZ, double* x, BState st,
+                      const int32_t* __restrict__ sys_of_tile, int m, int64_t total) {
+    bzy_range<NR>(Z, ldZ, x, st, sys_of_tile, m, total,
+                  (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
+}
+
 // After a true residual: beta per solve, relres, the next cycle's g[0],
 // the scale of V_0, and which solves take steps in the next cycle.
-__global__ void k_bcycle(BState st, int nsolve, int m, const double* nrm2, double tol,
-                         int first) {
-    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sv >= nsolve) return;
+__device__ __forceinline__ void bcycle_one(int sv, const BState& st, int m, const double* nrm2,
+                                           double tol, int first) {
     const double beta = sqrt(fmax(nrm2[sv], 0.0));
     if (first) st.bnorm[sv] = beta;
     if (!first) st.iters[sv] += st.ksteps[sv];
@@ -505,6 +582,12 @@ __global__ void k_bcycle(BState st, int nsolve, int m, const double* nrm2, doubl
     const bool go = bn > 0.0 && rel > tol && isfinite(rel);
     st.active[sv] = go ? 1 : 0;
     st.inv[sv] = (go && beta > 0.0) ? 1.0 / beta : 0.0;
+}
+
+__global__ void k_bcycle(BState st, int nsolve, int m, const double* nrm2, double tol,
+                         int first) {
+    const int sv = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sv < nsolve) bcycle_one(sv, st, m, nrm2, tol, first);
 }
 
 // ---------------------------------------------------------------------------
@@ -559,6 +642,259 @@ __global__ void k_cast32(const float* x, double* y, int64_t n) {
          e += (int64_t)gridDim.x * blockDim.x)
         y[e] = (double)x[e];
 }
+
+// ---------------------------------------------------------------------------
+// The whole solve in one persistent launch
+// ---------------------------------------------------------------------------
+//
+// k_bpersist runs every restart cycle of every solve of the batch: the same
+// phases as the per-cycle graph (FP32 cast, the Algorithm 3 root steps, the
+// FP64 operator product, the CGS2 unit passes, the Givens updates, the
+// scaling; at a cycle's end the back substitution, x += Z y, the true
+// residual and the restart), each phase a loop of the CTA over virtual
+// blocks, the phases separated by grid-wide barriers.  It is launched
+// cooperatively, so every CTA is resident and the barriers cannot wait for
+// a CTA that has not started.  Each barrier wait is bounded by a time limit;
+// a CTA whose wait runs out raises the shared error flag and returns, and
+// every other CTA returns at its next barrier (PPG_ERR_TIMEOUT on the host).
+// The FP32 root steps run on row groups of `rows` threads (64, 128 or 256,
+// the autotuned row tiling), several groups per CTA, each on its own tile
+// with its own staging slice and named barrier.
+
+struct GridBar {
+    unsigned count;   // CTAs arrived at the current barrier
+    unsigned gen;     // barriers completed
+    unsigned err;     // a wait ran out
+    unsigned pad;
+};
+
+struct PArgs {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const double* v64;
+    const float* v32;
+    const int32_t* sys_of_tile;
+    const int32_t* unit_tile0;
+    const int32_t* unit0;
+    const int32_t* sys_of_unit;
+    const int32_t* cta0;
+    int nsys, m, ldh, K, max_cycles, rows;
+    int64_t N, nunits, ntiles;
+    double tol;
+    double* V;
+    float* Z;
+    float *fa, *fb, *fc, *x32;
+    double* zd;
+    double* X;
+    double* Bp;
+    double* part;
+    int64_t pstr;
+    double *h1, *h2, *nrm;
+    const BStep* steps_p;
+    const BStep* steps_spmv;
+    const BStep* steps_resid;
+    BState st;
+    GridBar* bar;
+    unsigned long long timeout_ns;
+    int32_t* cycles_out;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch.  Thread 0 of each CTA arrives
+// on the counter; the last to arrive resets it and advances the
+// generation, the others wait for the generation to move, at most
+// timeout_ns (and a bounded number of polls).  Returns false, uniformly
+// over the CTA, when this or any other CTA's wait ran out.
+__device__ bool grid_sync(GridBar* gb, unsigned long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &gb->gen;
+        volatile unsigned* verr = &gb->err;
+        int ok = 1;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            for (unsigned it = 0; *vgen == g0; ++it) {
+                if (*verr != 0u) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > timeout_ns || it > (1u << 28)) {
+                    atomicExch(&gb->err, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (*verr != 0u) ok = 0;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// does any solve still take steps?  (all CTAs read the same array after a
+// barrier, so the answer is uniform over the grid)
+__device__ __forceinline__ bool any_active(const int32_t* active, int nsolve) {
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < nsolve; i += blockDim.x) mine |= active[i];
+    if (mine) s_any = 1;
+    __syncthreads();
+    const bool r = s_any != 0;
+    __syncthreads();
+    return r;
+}
+
+#define PSYNC()                                             \
+    do {                                                    \
+        if (!grid_sync(a.bar, a.timeout_ns)) return;        \
+    } while (0)
+
+template <int NR>
+__global__ void __launch_bounds__(256, 2) k_bpersist(const PArgs a) {
+    // staging shared by the root-step phases (FP32: values then columns,
+    // sliced per row group; FP64: the whole CTA)
+    __shared__ __align__(16) unsigned char sraw[BCHUNK * (8 + 4)];
+    __shared__ int32_t srp[BT + 8];
+    __shared__ double sred[8][NR];
+    __shared__ double bd_sred[8][BCH][NR];
+    __shared__ double bs_sh[ORTHO_MAXC][NR];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int nsolve = a.nsys * NR;
+    const int64_t total = a.N * NR;
+    const int64_t ldV = total;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + tid;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    const int rows = a.rows;
+    const int groups = 256 / rows;
+    const int group = tid / rows, gt = tid % rows;
+    const int fchunk = BCHUNK * rows / 256;
+    float* fsval = reinterpret_cast<float*>(sraw) + group * fchunk;
+    int32_t* fscol = reinterpret_cast<int32_t*>(sraw + BCHUNK * 4) + group * fchunk;
+    int32_t* fsrp = srp + group * (rows + 1);
+    double* dsval = reinterpret_cast<double*>(sraw);
+    int32_t* dscol = reinterpret_cast<int32_t*>(sraw + BCHUNK * 8);
+    const int64_t nvb_f = a.N / 256;   // CTA iterations of a root step: `groups` tiles each
+    int cycles = 0;
+    for (int cyc = 0; cyc < a.max_cycles; ++cyc) {
+        if (!any_active(a.st.active, nsolve)) break;
+        ++cycles;
+        for (int j = 0; j < a.m; ++j) {
+            double* vj = a.V + (size_t)j * ldV;
+            double* w = a.V + (size_t)(j + 1) * ldV;
+            float* zj = a.Z + (size_t)j * ldV;
+            for (int64_t e = gtid; e < total; e += gstride) a.x32[e] = (float)vj[e];
+            PSYNC();
+            // z_j = p(A) v_j: Algorithm 3 in FP32, one pass per step
+            BufSet<float> fs{};
+            fs.p[B_IN] = a.x32;
+            fs.p[B_P] = zj;
+            fs.p[B_A] = a.fa;
+            fs.p[B_B] = a.fb;
+            fs.p[B_C] = a.fc;
+            for (int k = 0; k < a.K; ++k) {
+                const BStep* steps = a.steps_p + (size_t)k * a.nsys;
+                for (int64_t vb = blockIdx.x; vb < nvb_f; vb += gridDim.x) {
+                    bstep_tile<float, NR>(vb * groups + group, rows, gt, group, fsval, fscol, fsrp,
+                                          fchunk, sred, a.rowptr, a.colind, a.v32, steps,
+                                          a.sys_of_tile, fs, nullptr, a.st.active);
+                    __syncthreads();
+                }
+                PSYNC();
+            }
+            for (int64_t e = gtid; e < total; e += gstride) a.zd[e] = (double)zj[e];
+            PSYNC();
+            // w = A z_j in FP64
+            BufSet<double> ds{};
+            ds.p[B_IN] = a.zd;
+            ds.p[B_OUT] = w;
+            for (int64_t vb = blockIdx.x; vb < a.ntiles; vb += gridDim.x) {
+                bstep_tile<double, NR>(vb, 256, tid, 0, dsval, dscol, srp, BCHUNK, sred, a.rowptr,
+                                       a.colind, a.v64, a.steps_spmv, a.sys_of_tile, ds, nullptr,
+                                       a.st.active);
+                __syncthreads();
+            }
+            PSYNC();
+            // CGS2 over the j + 1 basis columns, per unit, reduced per system
+            const int ncol = j + 1;
+            const int nch = (ncol + BCH - 1) / BCH;
+            for (int pass = 0; pass < 2; ++pass) {
+                double* h = pass == 0 ? a.h1 : a.h2;
+                for (int64_t vb = blockIdx.x; vb < a.nunits * nch; vb += gridDim.x) {
+                    bdot_block<NR>((int)(vb % a.nunits), (int)(vb / a.nunits), bd_sred, a.V, ldV,
+                                   ncol, w, 0, a.part, a.pstr, a.unit_tile0, a.sys_of_unit,
+                                   a.st.active);
+                    __syncthreads();
+                }
+                PSYNC();
+                const int nseg = a.nsys * ((ncol + 7) / 8);
+                for (int vb = blockIdx.x; vb < nseg; vb += gridDim.x)
+                    bsegsum_block(vb % a.nsys, vb / a.nsys, a.part, a.pstr, ncol, NR, a.unit0,
+                                  a.nsys, h);
+                PSYNC();
+                for (int64_t vb = blockIdx.x; vb < a.nunits; vb += gridDim.x) {
+                    bsub_block<NR>((int)vb, bs_sh, sred, a.V, ldV, ncol, w, h, nsolve,
+                                   a.unit_tile0, a.sys_of_unit, pass == 1, a.part, a.st.active);
+                    __syncthreads();
+                }
+                PSYNC();
+            }
+            for (int vb = blockIdx.x; vb < a.nsys; vb += gridDim.x)
+                bsegsum_block(vb, 0, a.part, NR, 1, NR, a.unit0, a.nsys, a.nrm);
+            PSYNC();
+            for (int64_t sv = gtid; sv < nsolve; sv += gstride)
+                bgivens_one((int)sv, a.st, nsolve, a.ldh, a.m, j, a.h1, a.h2, a.nrm, 0, a.tol);
+            PSYNC();
+            bscale_range<NR>(w, a.st.inv, a.sys_of_tile, total, gtid, gstride);
+            PSYNC();
+            if (!any_active(a.st.active, nsolve)) break;
+        }
+        // end of the cycle: y = R^-1 g, x += Z y, r = b - A x, restart
+        for (int64_t sv = gtid >> 5; sv < nsolve; sv += gstride >> 5)
+            bbacksolve_warp((int)sv, lane, a.st, a.ldh, a.m);
+        PSYNC();
+        bzy_range<NR>(a.Z, ldV, a.X, a.st, a.sys_of_tile, a.m, total, gtid, gstride);
+        PSYNC();
+        BufSet<double> rs{};
+        rs.p[B_IN] = a.X;
+        rs.p[B_P] = a.Bp;
+        rs.p[B_OUT] = a.V;
+        for (int64_t vb = blockIdx.x; vb < a.ntiles; vb += gridDim.x) {
+            bstep_tile<double, NR>(vb, 256, tid, 0, dsval, dscol, srp, BCHUNK, sred, a.rowptr,
+                                   a.colind, a.v64, a.steps_resid, a.sys_of_tile, rs, a.part,
+                                   nullptr);
+            __syncthreads();
+        }
+        PSYNC();
+        for (int vb = blockIdx.x; vb < a.nsys; vb += gridDim.x)
+            bsegsum_block(vb, 0, a.part, NR, 1, NR, a.cta0, a.nsys, a.nrm);
+        PSYNC();
+        for (int64_t sv = gtid; sv < nsolve; sv += gstride)
+            bcycle_one((int)sv, a.st, a.m, a.nrm, a.tol, 0);
+        PSYNC();
+        bscale_range<NR>(a.V, a.st.inv, a.sys_of_tile, total, gtid, gstride);
+        PSYNC();
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.cycles_out = cycles;
+}
+
+#undef PSYNC
 
 // ---------------------------------------------------------------------------
 // host side
@@ -633,6 +969,8 @@ struct Work {
     BStep* steps_resid; // [nsys]
     BStep* steps_build; // [nsys] SpMV for the construction
     BState st;
+    GridBar* gbar;      // grid barrier of the persistent launch
+    int32_t* cyc;       // cycles the persistent launch ran
 };
 
 template <int NR>
@@ -758,6 +1096,113 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
     return PPG_OK;
 }
 
+// The whole solve as one persistent cooperative launch (captured as a
+// one-node CUDA graph on a non-legacy stream).  Returns after the stream
+// has synchronised; *cycles_out = restart cycles run.
+template <int NR>
+int32_t run_persistent(const Batch& B, Work& W, int K, double tol, int max_cycles,
+                       double timeout_ms, cudaStream_t s, int* cycles_out) {
+    PArgs a{};
+    a.rowptr = B.rowptr;
+    a.colind = B.colind;
+    a.v64 = B.v64;
+    a.v32 = B.v32;
+    a.sys_of_tile = B.sys_of_tile;
+    a.unit_tile0 = B.unit_tile0;
+    a.unit0 = B.unit0;
+    a.sys_of_unit = B.sys_of_unit;
+    a.cta0 = B.cta0;
+    a.nsys = B.nsys;
+    a.m = B.m;
+    a.ldh = B.ldh;
+    a.K = K;
+    a.max_cycles = max_cycles;
+    a.rows = B.rows_per_cta;
+    a.N = B.N;
+    a.nunits = B.nunits;
+    a.ntiles = B.ntiles;
+    a.tol = tol;
+    a.V = W.V;
+    a.Z = W.Z;
+    a.fa = W.fa;
+    a.fb = W.fb;
+    a.fc = W.fc;
+    a.x32 = W.v32;
+    a.zd = W.zd;
+    a.X = W.X;
+    a.Bp = W.Bp;
+    a.part = W.part;
+    a.pstr = W.pstr;
+    a.h1 = W.h1;
+    a.h2 = W.h2;
+    a.nrm = W.nrm;
+    a.steps_p = W.steps_p;
+    a.steps_spmv = W.steps_spmv;
+    a.steps_resid = W.steps_resid;
+    a.st = W.st;
+    a.bar = W.gbar;
+    a.timeout_ns = (unsigned long long)(std::max(0.0, timeout_ms) * 1e6);
+    a.cycles_out = W.cyc;
+    if (a.rows != 64 && a.rows != 128 && a.rows != 256) return PPG_ERR_ARG;
+    int occ = 0;
+    PPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpersist<NR>, 256, 0));
+    if (occ < 1) {
+        set_cuda_error(cudaErrorInvalidConfiguration, "k_bpersist: no resident CTA");
+        return PPG_ERR_CUDA;
+    }
+    // every CTA resident (cooperative launch); no more CTAs than tiles
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)occ * device_sm_count(), B.ntiles));
+    PPG_CUDA(cudaMemsetAsync(W.gbar, 0, sizeof(GridBar), s));
+    PPG_CUDA(cudaMemsetAsync(W.cyc, 0, sizeof(int32_t), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    bool launched = false;
+    if (s != nullptr) {
+        cudaStreamCaptureStatus cs;
+        PPG_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return PPG_ERR_ARG;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t gexec = nullptr;
+        PPG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t el = cudaLaunchKernelEx(&cfg, k_bpersist<NR>, a);
+        const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+        if (el == cudaSuccess && ee == cudaSuccess &&
+            cudaGraphInstantiate(&gexec, graph, 0) == cudaSuccess) {
+            const cudaError_t eg = cudaGraphLaunch(gexec, s);
+            const cudaError_t es = cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(gexec);
+            cudaGraphDestroy(graph);
+            if (eg != cudaSuccess) { set_cuda_error(eg, "cudaGraphLaunch(k_bpersist)"); return PPG_ERR_CUDA; }
+            if (es != cudaSuccess) { set_cuda_error(es, "k_bpersist"); return PPG_ERR_CUDA; }
+            launched = true;
+        } else {
+            // this runtime cannot capture the cooperative launch: launch it directly
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+        }
+    }
+    if (!launched) {
+        PPG_CUDA(cudaLaunchKernelEx(&cfg, k_bpersist<NR>, a));
+        PPG_CUDA(cudaStreamSynchronize(s));
+    }
+    ++g_launches;
+    GridBar gb{};
+    int32_t cyc = 0;
+    PPG_CUDA(cudaMemcpy(&gb, W.gbar, sizeof(GridBar), cudaMemcpyDeviceToHost));
+    PPG_CUDA(cudaMemcpy(&cyc, W.cyc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *cycles_out = cyc;
+    return gb.err ? PPG_ERR_TIMEOUT : PPG_OK;
+}
+
 }  // namespace
 }  // namespace ppg
 
@@ -854,6 +1299,8 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     ar.add(&W.st.ksteps, (size_t)nsolve);
     ar.add(&W.st.iters, (size_t)nsolve);
     ar.add(&W.st.brk, (size_t)nsolve);
+    ar.add(&W.gbar, 1);
+    ar.add(&W.cyc, 1);
     PPG_TRY(ar.alloc(s));
     struct Guard { Arena& a; cudaStream_t s; ~Guard() { a.release(s); } } guard{ar, s};
 
@@ -1022,59 +1469,14 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     Bs.m = m;
     Bs.ldh = m + 1;
 
-    // capture one restart cycle as a graph (not possible on the legacy
-    // default stream: there the cycle is launched directly)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    int64_t launches_per_cycle = 0;
-    if (s != nullptr) {
-        cudaStreamCaptureStatus cs;
-        PPG_CUDA(cudaStreamIsCapturing(s, &cs));
-        if (cs != cudaStreamCaptureStatusNone) return PPG_ERR_ARG;
-        PPG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const int64_t l0 = g_launches;
-        int32_t rc = cycle_batch<NR>(Bs, W, K, tol, s);
-        const int64_t per_cycle = g_launches - l0;
-        g_launches = l0;
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
-        if (rc < 0) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (e != cudaSuccess) {
-            set_cuda_error(e, "cudaStreamEndCapture");
-            return PPG_ERR_CUDA;
-        }
-        e = cudaGraphInstantiate(&gexec, graph, 0);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(graph);
-            set_cuda_error(e, "cudaGraphInstantiate");
-            return PPG_ERR_CUDA;
-        }
-        launches_per_cycle = per_cycle;
-    }
-    struct GGuard {
-        cudaGraph_t g;
-        cudaGraphExec_t x;
-        ~GGuard() {
-            if (x) cudaGraphExecDestroy(x);
-            if (g) cudaGraphDestroy(g);
-        }
-    } gg{graph, gexec};
-
     std::vector<double> rel(nsolve);
     std::vector<int32_t> act(nsolve);
     const int max_cycles = o->max_cycles > 0 ? o->max_cycles : 10000;
     int cycles = 0;
     bool all = false;
-    while (cycles < max_cycles) {
-        if (gexec) {
-            PPG_CUDA(cudaGraphLaunch(gexec, s));
-            g_launches += launches_per_cycle;
-        } else {
-            PPG_TRY(cycle_batch<NR>(Bs, W, K, tol, s));
-        }
-        ++cycles;
+    if (o->batch_mode == 0) {
+        // every cycle of every solve in one persistent launch
+        PPG_TRY(run_persistent<NR>(Bs, W, K, tol, max_cycles, o->wait_timeout_ms, s, &cycles));
         PPG_CUDA(cudaMemcpyAsync(rel.data(), W.st.relres, sizeof(double) * nsolve,
                                  cudaMemcpyDeviceToHost, s));
         PPG_CUDA(cudaMemcpyAsync(act.data(), W.st.active, sizeof(int32_t) * nsolve,
@@ -1085,7 +1487,66 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
             if (!std::isfinite(rel[i])) return PPG_ERR_NONFINITE;
             if (act[i]) all = false;
         }
-        if (all) break;
+    } else {
+        // capture one restart cycle as a graph (not possible on the legacy
+        // default stream: there the cycle is launched directly)
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t gexec = nullptr;
+        int64_t launches_per_cycle = 0;
+        if (s != nullptr) {
+            cudaStreamCaptureStatus cs;
+            PPG_CUDA(cudaStreamIsCapturing(s, &cs));
+            if (cs != cudaStreamCaptureStatusNone) return PPG_ERR_ARG;
+            PPG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const int64_t l0 = g_launches;
+            int32_t rc = cycle_batch<NR>(Bs, W, K, tol, s);
+            const int64_t per_cycle = g_launches - l0;
+            g_launches = l0;
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (rc < 0) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) {
+                set_cuda_error(e, "cudaStreamEndCapture");
+                return PPG_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&gexec, graph, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                set_cuda_error(e, "cudaGraphInstantiate");
+                return PPG_ERR_CUDA;
+            }
+            launches_per_cycle = per_cycle;
+        }
+        struct GGuard {
+            cudaGraph_t g;
+            cudaGraphExec_t x;
+            ~GGuard() {
+                if (x) cudaGraphExecDestroy(x);
+                if (g) cudaGraphDestroy(g);
+            }
+        } gg{graph, gexec};
+        while (cycles < max_cycles) {
+            if (gexec) {
+                PPG_CUDA(cudaGraphLaunch(gexec, s));
+                g_launches += launches_per_cycle;
+            } else {
+                PPG_TRY(cycle_batch<NR>(Bs, W, K, tol, s));
+            }
+            ++cycles;
+            PPG_CUDA(cudaMemcpyAsync(rel.data(), W.st.relres, sizeof(double) * nsolve,
+                                     cudaMemcpyDeviceToHost, s));
+            PPG_CUDA(cudaMemcpyAsync(act.data(), W.st.active, sizeof(int32_t) * nsolve,
+                                     cudaMemcpyDeviceToHost, s));
+            PPG_CUDA(cudaStreamSynchronize(s));
+            all = true;
+            for (int i = 0; i < nsolve; ++i) {
+                if (!std::isfinite(rel[i])) return PPG_ERR_NONFINITE;
+                if (act[i]) all = false;
+            }
+            if (all) break;
+        }
     }
     // ---- unpack ----
     for (int i = 0; i < nsys; ++i) {

@@ -322,31 +322,30 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     return false;
 }
 
-__global__ void __launch_bounds__(ORTHO_THREADS, 2)
-k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
-          const double* __restrict__ h1, double* part, unsigned* counter, double* hout,
-          unsigned* err) {
-    extern __shared__ __align__(128) double sd_stage[];   // 2 x ncol x SD_R
-    __shared__ __align__(16) double spart[ORTHO_WARPS][SD_R];
-    __shared__ __align__(16) double ws[SD_R];
-    __shared__ __align__(8) uint64_t bar[2];
+// Shared-memory layout of k_sub_dot besides the staged tiles.
+struct SubDotShared {
+    double spart[ORTHO_WARPS][SD_R];
+    double ws[SD_R];
+    uint64_t bar[2];
+};
+
+// The tile loop of k_sub_dot for a warp owning NC columns (a compile-time
+// count: on GB300 a predicated or discarded FP64 multiply-add still takes
+// its FP64 pipe slot, so missing columns must not appear in the code).
+// Warps of one CTA may run different instantiations; they meet at the same
+// barriers.
+template <int NC>
+__device__ __forceinline__ void sub_dot_tiles(const double* __restrict__ V, int64_t ldv, int ncol,
+                                              double* w, int32_t n, const double* __restrict__ h1,
+                                              double* part, unsigned* counter, double* hout,
+                                              unsigned* err, double* sd_stage,
+                                              SubDotShared& sm, int c0) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t stage_elems = (int64_t)ncol * SD_R;
     const int ntiles = (int)(((int64_t)n + SD_R - 1) / SD_R);
-    // this warp's columns [c0, c0 + nc), near-equal runs
-    const int c0 = warp * ncol / ORTHO_WARPS;
-    const int nc = (warp + 1) * ncol / ORTHO_WARPS - c0;
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    PPG_PDL_TRIGGER();
-    PPG_PDL_WAIT();   // h1 and w come from the kernels before this one
-    double hreg[SD_CPW];
+    double hreg[NC > 0 ? NC : 1];
 #pragma unroll
-    for (int k = 0; k < SD_CPW; ++k) hreg[k] = k < nc ? h1[c0 + k] : 0.0;
-    __syncthreads();
+    for (int k = 0; k < NC; ++k) hreg[k] = h1[c0 + k];
 
     // thread 0: tile t into stage st (rows up to the padded column length,
     // a multiple of 64 rows, so every copy is a whole number of 16 bytes)
@@ -354,7 +353,7 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
         const int64_t r0 = (int64_t)t * SD_R;
         const int64_t rows = min((int64_t)SD_R, ldv - r0);
         const uint32_t bytes = (uint32_t)(rows * 8);
-        const uint32_t b = smem_u32(&bar[st]);
+        const uint32_t b = smem_u32(&sm.bar[st]);
         double* dst = sd_stage + st * stage_elems;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
                      "r"(bytes * (uint32_t)ncol)
@@ -373,9 +372,9 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
         if (first + step < ntiles) issue(first + step, 1);
     }
 
-    double acc[SD_CPW];
+    double acc[NC > 0 ? NC : 1];
 #pragma unroll
-    for (int k = 0; k < SD_CPW; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NC; ++k) acc[k] = 0.0;
     int k_local = 0;
     bool ok = true;
     for (int t = first; t < ntiles; t += step, ++k_local) {
@@ -391,7 +390,8 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
                 wv.x = w[gw];
             }
         }
-        const bool mine = mbar_wait_bounded(smem_u32(&bar[st]), (uint32_t)((k_local >> 1) & 1));
+        const bool mine =
+            mbar_wait_bounded(smem_u32(&sm.bar[st]), (uint32_t)((k_local >> 1) & 1));
         if (!__syncthreads_and(mine)) {
             ok = false;
             break;
@@ -399,36 +399,32 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
         const double* S = sd_stage + st * stage_elems;
         // this thread's register block; rows at or past n hold the basis's
         // padding (never written, possibly not finite) and become zeros
-        double2 va[SD_CPW], vb[SD_CPW];
+        double2 va[NC > 0 ? NC : 1], vb[NC > 0 ? NC : 1];
         const bool full = r0 + SD_R <= n;
         const int64_t ra = r0 + 2 * lane, rb = r0 + 64 + 2 * lane;
 #pragma unroll
-        for (int k = 0; k < SD_CPW; ++k) {
-            if (k < nc) {   // uniform over the warp: no FMA for a missing column
-                va[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 2 * lane);
-                vb[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 64 + 2 * lane);
-                if (!full) {
-                    va[k].x = ra < n ? va[k].x : 0.0;
-                    va[k].y = ra + 1 < n ? va[k].y : 0.0;
-                    vb[k].x = rb < n ? vb[k].x : 0.0;
-                    vb[k].y = rb + 1 < n ? vb[k].y : 0.0;
-                }
+        for (int k = 0; k < NC; ++k) {
+            va[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 2 * lane);
+            vb[k] = *reinterpret_cast<const double2*>(S + (c0 + k) * SD_R + 64 + 2 * lane);
+            if (!full) {
+                va[k].x = ra < n ? va[k].x : 0.0;
+                va[k].y = ra + 1 < n ? va[k].y : 0.0;
+                vb[k].x = rb < n ? vb[k].x : 0.0;
+                vb[k].y = rb + 1 < n ? vb[k].y : 0.0;
             }
         }
         // phase 1: row partials of V h1 over this warp's columns
         {
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
 #pragma unroll
-            for (int k = 0; k < SD_CPW; ++k) {
-                if (k < nc) {
-                    s0 = fma(va[k].x, hreg[k], s0);
-                    s1 = fma(va[k].y, hreg[k], s1);
-                    s2 = fma(vb[k].x, hreg[k], s2);
-                    s3 = fma(vb[k].y, hreg[k], s3);
-                }
+            for (int k = 0; k < NC; ++k) {
+                s0 = fma(va[k].x, hreg[k], s0);
+                s1 = fma(va[k].y, hreg[k], s1);
+                s2 = fma(vb[k].x, hreg[k], s2);
+                s3 = fma(vb[k].y, hreg[k], s3);
             }
-            *reinterpret_cast<double2*>(&spart[warp][2 * lane]) = make_double2(s0, s1);
-            *reinterpret_cast<double2*>(&spart[warp][64 + 2 * lane]) = make_double2(s2, s3);
+            *reinterpret_cast<double2*>(&sm.spart[warp][2 * lane]) = make_double2(s0, s1);
+            *reinterpret_cast<double2*>(&sm.spart[warp][64 + 2 * lane]) = make_double2(s2, s3);
         }
         __syncthreads();   // the stage is in registers; the partials are complete
         if (tid == 0 && t + 2 * step < ntiles) {
@@ -442,13 +438,13 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
             double sa = 0.0, sb = 0.0;
 #pragma unroll
             for (int g = 0; g < ORTHO_WARPS; ++g) {
-                sa += spart[g][r];
-                sb += spart[g][r + 1];
+                sa += sm.spart[g][r];
+                sb += sm.spart[g][r + 1];
             }
             double2 o;
             o.x = gw < n ? wv.x - sa : 0.0;
             o.y = gw + 1 < n ? wv.y - sb : 0.0;
-            *reinterpret_cast<double2*>(ws + r) = o;
+            *reinterpret_cast<double2*>(sm.ws + r) = o;
             if (gw + 1 < n) {
                 *reinterpret_cast<double2*>(w + gw) = o;
             } else if (gw < n) {
@@ -458,16 +454,14 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
         __syncthreads();
         // phase 2: column partials of V^T w' over this lane's four rows
         {
-            const double2 wa = *reinterpret_cast<const double2*>(ws + 2 * lane);
-            const double2 wb = *reinterpret_cast<const double2*>(ws + 64 + 2 * lane);
+            const double2 wa = *reinterpret_cast<const double2*>(sm.ws + 2 * lane);
+            const double2 wb = *reinterpret_cast<const double2*>(sm.ws + 64 + 2 * lane);
 #pragma unroll
-            for (int k = 0; k < SD_CPW; ++k) {
-                if (k < nc) {
-                    acc[k] = fma(va[k].x, wa.x, acc[k]);
-                    acc[k] = fma(va[k].y, wa.y, acc[k]);
-                    acc[k] = fma(vb[k].x, wb.x, acc[k]);
-                    acc[k] = fma(vb[k].y, wb.y, acc[k]);
-                }
+            for (int k = 0; k < NC; ++k) {
+                acc[k] = fma(va[k].x, wa.x, acc[k]);
+                acc[k] = fma(va[k].y, wa.y, acc[k]);
+                acc[k] = fma(vb[k].x, wb.x, acc[k]);
+                acc[k] = fma(vb[k].y, wb.y, acc[k]);
             }
         }
     }
@@ -479,24 +473,57 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
             for (int j = 0; j < 2; ++j) {
                 const int kk = k_local + j;   // outstanding tiles k_local, k_local + 1
                 if (first + kk * step < ntiles)
-                    mbar_wait_bounded(smem_u32(&bar[kk & 1]), (uint32_t)((kk >> 1) & 1));
+                    mbar_wait_bounded(smem_u32(&sm.bar[kk & 1]), (uint32_t)((kk >> 1) & 1));
             }
         }
         return;
     }
     // per-CTA partial sums of each column over this CTA's rows
 #pragma unroll
-    for (int k = 0; k < SD_CPW; ++k) {
-        if (k < nc) {
-            const double v = warp_sum(acc[k]);
-            if (lane == 0) part[(size_t)blockIdx.x * PART_STRIDE + c0 + k] = v;
-        }
+    for (int k = 0; k < NC; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) part[(size_t)blockIdx.x * PART_STRIDE + c0 + k] = v;
     }
     if (last_block_done(counter)) {
         __threadfence();
         final_reduce(part, gridDim.x, ncol, hout);
         if (tid == 0) *counter = 0u;
     }
+}
+
+__global__ void __launch_bounds__(ORTHO_THREADS, 2)
+k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
+          const double* __restrict__ h1, double* part, unsigned* counter, double* hout,
+          unsigned* err) {
+    extern __shared__ __align__(128) double sd_stage[];   // 2 x ncol x SD_R
+    __shared__ __align__(16) SubDotShared sm;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // this warp's columns [c0, c0 + nc), near-equal runs
+    const int c0 = warp * ncol / ORTHO_WARPS;
+    const int nc = (warp + 1) * ncol / ORTHO_WARPS - c0;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    PPG_PDL_TRIGGER();
+    PPG_PDL_WAIT();   // h1 and w come from the kernels before this one
+    __syncthreads();
+#define PPG_SD_CASE(K)                                                                      \
+    case K:                                                                                 \
+        sub_dot_tiles<K>(V, ldv, ncol, w, n, h1, part, counter, hout, err, sd_stage, sm, c0); \
+        break;
+    switch (nc) {   // uniform over the warp
+        PPG_SD_CASE(0)
+        PPG_SD_CASE(1)
+        PPG_SD_CASE(2)
+        PPG_SD_CASE(3)
+        PPG_SD_CASE(4)
+        PPG_SD_CASE(5)
+        PPG_SD_CASE(6)
+        default: sub_dot_tiles<7>(V, ldv, ncol, w, n, h1, part, counter, hout, err, sd_stage, sm, c0);
+    }
+#undef PPG_SD_CASE
 }
 
 // CTAs of a kernel resident at once on the current device (occupancy x

@@ -27,7 +27,7 @@ def _roots_close(got, ref, tol):
     return np.max(C[r, c] / np.abs(ref[c])) <= tol
 
 
-def _run(p, torch, probs, d, m, tol, nrhs, side_stream):
+def _run(p, torch, probs, d, m, tol, nrhs, side_stream, **kw):
     As = [dev_csr(p, torch, A) for A, _, _ in probs]
     Bs = [to_dev(torch, np.ascontiguousarray(B[:nrhs])) for _, B, _ in probs]
     v0s = [to_dev(torch, v0) for _, _, v0 in probs]
@@ -35,10 +35,10 @@ def _run(p, torch, probs, d, m, tol, nrhs, side_stream):
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            Xs, info = p.solve_batched(As, Bs, v0s, d, m, tol)
+            Xs, info = p.solve_batched(As, Bs, v0s, d, m, tol, **kw)
         torch.cuda.current_stream().wait_stream(s)
     else:
-        Xs, info = p.solve_batched(As, Bs, v0s, d, m, tol)
+        Xs, info = p.solve_batched(As, Bs, v0s, d, m, tol, **kw)
     torch.cuda.synchronize()
     return [x.cpu().numpy() for x in Xs], info
 
@@ -88,3 +88,49 @@ def test_batched_full_size_64_systems_4_rhs(env):
         A, _, v0 = probs[s]
         orc = poly.build_poly(A.to_scipy(), d, v0)
         assert _roots_close(info["roots"][s].complex(), orc.roots, 1e-8)
+
+
+@pytest.mark.parametrize("side_stream", [True, False])
+def test_batched_mid_size_persistent_launch_against_graph_and_oracle(env, side_stream):
+    """Eight systems with sides 64-200 (full 8-tile CGS2 units, up to 157
+    tiles per system), 4 right-hand sides: the persistent launch gives
+    exactly the per-cycle graph's results (the same arithmetic, phase by
+    phase), and every one of the 32 solves matches the oracle's float32-inner
+    FGMRES: iterations within 2, solution within 1e-6."""
+    p, torch = env
+    probs = synth.batch_problem(nsys=8, seed=41, side_lo=64, side_hi=200, nrhs=4)
+    d, m, tol = 12, 30, 1e-10
+    Xp, ip = _run(p, torch, probs, d, m, tol, 4, side_stream, persistent=True)
+    Xg, ig = _run(p, torch, probs, d, m, tol, 4, side_stream, persistent=False)
+    assert ip["status"] == 0 and ig["status"] == 0
+    assert ip["stats"]["cycles"] == ig["stats"]["cycles"]
+    assert np.array_equal(ip["iters"], ig["iters"])
+    for s in range(len(probs)):
+        assert np.array_equal(Xp[s], Xg[s])
+    for s, (A, B, v0) in enumerate(probs):
+        As = A.to_scipy()
+        R = ip["roots"][s]
+        for k in range(4):
+            rel = np.linalg.norm(B[k] - As @ Xp[s][k]) / np.linalg.norm(B[k])
+            assert rel <= tol
+            xo, so = gmres.fgmres_p(As, R.complex(), B[k], m, tol, inner="f32")
+            assert abs(int(ip["iters"][s, k]) - so.iters) <= 2
+            assert np.linalg.norm(Xp[s][k] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_batched_persistent_wait_limit_returns_timeout(env):
+    """Every grid-wide wait of the persistent launch is bounded: with a zero
+    limit the first barrier's waits run out, every CTA returns and the call
+    reports PPG_ERR_TIMEOUT; the context stays usable and the next call,
+    with the default limit, solves the batch."""
+    p, torch = env
+    probs = synth.batch_problem(nsys=6, seed=7, side_lo=9, side_hi=40, nrhs=4)
+    with pytest.raises(p.PPGError) as ei:
+        _run(p, torch, probs, 8, 20, 1e-10, 4, True, wait_timeout_ms=0.0)
+    assert ei.value.code == -10
+    Xs, info = _run(p, torch, probs, 8, 20, 1e-10, 4, True)
+    assert info["status"] == 0
+    for s, (A, B, _) in enumerate(probs):
+        for k in range(4):
+            rel = np.linalg.norm(B[k] - A.to_scipy() @ Xs[s][k]) / np.linalg.norm(B[k])
+            assert rel <= 1e-10

@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(ppg):
     for name in declared:
         assert hasattr(ppg.lib, name), name
     assert declared == set(ppg.EXPORTS)
-    assert ppg.lib.ppg_abi_version() == 1
+    assert ppg.lib.ppg_abi_version() == 2
     assert ppg.lib.ppg_strerror(-3).decode() == "H_dd is singular"
 
 
@@ -165,7 +165,7 @@ int main(void) {
     ppg_opts o;
     double re[3] = {1.0, 4.0, 2.0}, im[3] = {0.0, 0.0, 0.0}, ro[3], io[3];
     ppg_default_opts(&o);
-    if (ppg_abi_version() != 1 || o.max_cycles <= 0) return 1;
+    if (ppg_abi_version() != 2 || o.max_cycles <= 0) return 1;
     if (ppg_leja_order(3, re, im, ro, io) != PPG_OK) return 2;
     /* the largest modulus first (modified Leja order) */
     if (ro[0] != 4.0) return 3;
