@@ -661,7 +661,10 @@ def run_profile_case(name):
     ``phi_cd2d_1000``: two applications of the benchmark's own polynomial;
     ``batched_64x4``: one call of the batching form on its full workload;
     ``batched_16x4``: the same with its first 16 systems;
-    ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix."""
+    ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix;
+    ``chain_phi_cd3d_160_f64`` / ``chain_p_cd3d_160_f32``: the 160^3 workload's
+    degree-60 polynomial applied once (Algorithm 1 in FP64 / Algorithm 3 in
+    FP32) after its construction, for in-chain captures."""
     import numpy as np
     import torch
 
@@ -711,6 +714,21 @@ def run_profile_case(name):
         Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals, dtype=torch.float32)
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda().float()
         y = ppg.apply_poly(Ad, roots, v)
+    elif name in ("chain_phi_cd3d_160_f64", "chain_p_cd3d_160_f32"):
+        # the precision workload's own degree-60 polynomial (60 SpMV launches
+        # of the construction), then one whole chain: Algorithm 1 in FP64 or
+        # Algorithm 3 in FP32; skipping 90 root-step launches lands mid-chain
+        P = synth.problem("cd3d_160")
+        A = P.A
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
+        R = ppg.build_poly(Ad, P.d, torch.from_numpy(P.v0).cuda())
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
+        if name == "chain_phi_cd3d_160_f64":
+            y = ppg.apply_phi(Ad, R, v)
+        else:
+            A32 = Ad.astype(torch.float32)
+            del Ad
+            y = ppg.apply_poly(A32, R, v.float())
     else:
         raise SystemExit("unknown profile case " + name)
     torch.cuda.synchronize()
