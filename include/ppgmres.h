@@ -98,7 +98,10 @@ typedef struct ppg_opts {
                                       solve in one persistent cooperative launch (default),
                                       1 = one CUDA graph per restart cycle, replayed by a
                                       host loop */
-    int32_t pad_;
+    int32_t cgs2_fused;            /* 1: run CGS2's second update and dot pass as one fused
+                                      pass over the basis (3/4 of the bytes, the same FP64
+                                      multiply-adds; measured slower on GB300, where the
+                                      FP64 pipe bounds CGS2); default 0 */
     double  wait_timeout_ms;       /* limit of each grid-wide barrier wait of the persistent
                                       launch (default 5000); a wait that runs out ends the
                                       launch with PPG_ERR_TIMEOUT */
@@ -348,6 +351,59 @@ int32_t ppg_build_poly_checked(const ppg_csr* A, int32_t d, const double* v0,
                                const double* b, double stch_tol, int32_t d_min,
                                const ppg_opts* opts, ppg_roots* out,
                                ppg_poly_check* info, void* stream);
+
+/* ---- Multi-root fused sweep (the matrix-powers idea of Section 1) ------- */
+
+/* A plan for applying Algorithm 3 in FP32 with both SpMV passes of each
+ * conjugate pair in one pass over the matrix.  The matrix is reordered
+ * symmetrically (row i of the plan's matrix is row perm[i] of A, its
+ * entries in their stored order, columns relabelled) so that consecutive
+ * tiles of tile_rows rows are compact; each tile's halo (the rows outside
+ * it that its rows reference) is listed.  A pair then runs as one launch:
+ * tmp = 2a prod - A prod over the tile and its halo into shared memory,
+ * then A tmp for the tile's rows.  Every row keeps the unfused arithmetic,
+ * so results are bit-identical to ppg_apply_poly on A.
+ *   A          PPG_F32 CSR (device), structurally suited to tiling (the
+ *              plan copies what it needs; A may be freed afterwards)
+ *   perm_host  HOST array of n row indices (new -> old), a permutation, or
+ *              NULL: rows are grouped by breadth-first growth over the
+ *              pattern of A from the lowest-numbered row not yet placed
+ *   tile_rows  rows per tile, a multiple of 32 in [32, 16384]
+ *   fuse       1: fuse pairs when the halos total at most 60 % of n and a
+ *              tile fits in shared memory; 0: never (the plain chain on the
+ *              reordered matrix, for comparison)
+ * The plan owns device memory (cudaMalloc, about the size of A plus 8n
+ * bytes) until ppg_sweep_plan_destroy.  Synchronises `stream`.  Errors:
+ * PPG_ERR_ARG (bad perm, tile_rows), PPG_ERR_CSR, PPG_ERR_NOMEM. */
+typedef struct ppg_sweep_plan ppg_sweep_plan;
+
+typedef struct ppg_sweep_info {
+    int32_t n, nnz, tile_rows, ntiles;
+    int32_t max_halo;       /* largest halo of one tile */
+    int32_t fused;          /* 1 when pairs run fused */
+    int64_t halo_total;     /* sum of the tiles' halo sizes */
+    double  halo_fraction;  /* halo_total / n */
+} ppg_sweep_info;
+
+int32_t ppg_sweep_plan_create(const ppg_csr* A, const int32_t* perm_host, int32_t tile_rows,
+                              int32_t fuse, ppg_sweep_plan** out, void* stream);
+int32_t ppg_sweep_plan_info(const ppg_sweep_plan* plan, ppg_sweep_info* info);
+void    ppg_sweep_plan_destroy(ppg_sweep_plan* plan);
+
+/* y = p(A) v (Algorithm 3, FP32 vectors in A's original ordering) through a
+ * plan: v is permuted into the plan's ordering, the chain runs with each
+ * non-final pair fused, and the result is permuted back.  Bit-identical to
+ * ppg_apply_poly on the plan's A.  Asynchronous. */
+int32_t ppg_apply_poly_sweep(const ppg_sweep_plan* plan, const ppg_roots* r, const void* v,
+                             void* y, void* stream);
+
+/* The precision form (as ppg_solve_flex) with z_j = p(A) v_j applied
+ * through a plan of the FP32 matrix: identical iterates to ppg_solve_flex
+ * with that matrix.  A64 PPG_F64 with the plan's n.  Synchronises. */
+int32_t ppg_solve_flex_sweep(const ppg_csr* A64, const ppg_sweep_plan* plan,
+                             const ppg_roots* r, const double* b, double* x, int32_t m,
+                             double tol, const ppg_opts* opts, ppg_stats* stats,
+                             void* stream);
 
 /* Transposed CSR of A (for the adjoint solve with A^T): rowptr_t [n+1],
  * colind_t [nnz], vals_t [nnz] in A's dtype, all device, caller-owned.

@@ -20,7 +20,7 @@ from ._binding import (EXPORTS, PPGError, Roots, add_roots, csr_validate_host,  
 try:  # the device API needs torch; the host-only steps above do not
     from .api import (CSR, PPGMRESFunction, adjoint_vals_grad, apply_phi,  # noqa: F401
                       apply_poly, apply_poly_noalloc, build_poly, build_poly_checked, build_poly_composite, solve, solve_batched, solve_chpoly, solve_double, solve_flex, solve_host, spmv,
-                      stability_check)
+                      stability_check, SweepPlan, solve_flex_sweep)
 except ImportError:  # pragma: no cover
     pass
 

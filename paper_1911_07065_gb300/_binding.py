@@ -43,7 +43,7 @@ class ppg_opts(C.Structure):
     _fields_ = [("max_cycles", c_i32), ("stability_control", c_i32),
                 ("pof_threshold_log10", c_f64), ("pof_step_log10", c_f64),
                 ("timing", c_i32), ("x0_given", c_i32), ("batch_mode", c_i32),
-                ("pad_", c_i32), ("wait_timeout_ms", c_f64)]
+                ("cgs2_fused", c_i32), ("wait_timeout_ms", c_f64)]
 
 
 class ppg_stats(C.Structure):
@@ -62,6 +62,15 @@ class ppg_poly_check(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class ppg_sweep_info(C.Structure):
+    _fields_ = [("n", c_i32), ("nnz", c_i32), ("tile_rows", c_i32), ("ntiles", c_i32),
+                ("max_halo", c_i32), ("fused", c_i32), ("halo_total", c_i64),
+                ("halo_fraction", c_f64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PPGError(RuntimeError):
@@ -95,6 +104,14 @@ def _load():
         "ppg_build_poly_checked": (c_i32, [C.POINTER(ppg_csr), c_i32, c_vp, c_vp, c_f64, c_i32,
                                            C.POINTER(ppg_opts), C.POINTER(ppg_roots),
                                            C.POINTER(ppg_poly_check), c_vp]),
+        "ppg_sweep_plan_create": (c_i32, [C.POINTER(ppg_csr), c_vp, c_i32, c_i32,
+                                          C.POINTER(c_vp), c_vp]),
+        "ppg_sweep_plan_info": (c_i32, [c_vp, C.POINTER(ppg_sweep_info)]),
+        "ppg_sweep_plan_destroy": (None, [c_vp]),
+        "ppg_apply_poly_sweep": (c_i32, [c_vp, C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
+        "ppg_solve_flex_sweep": (c_i32, [C.POINTER(ppg_csr), c_vp, C.POINTER(ppg_roots), c_vp,
+                                         c_vp, c_i32, c_f64, C.POINTER(ppg_opts),
+                                         C.POINTER(ppg_stats), c_vp]),
         "ppg_apply_poly": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
         "ppg_apply_phi": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp, c_vp, c_vp]),
         "ppg_apply_poly_noalloc": (c_i32, [C.POINTER(ppg_csr), C.POINTER(ppg_roots), c_vp,
@@ -140,7 +157,8 @@ EXPORTS = (
     "ppg_spmv", "ppg_solve", "ppg_solve_flex", "ppg_stability_check",
     "ppg_csr_transpose", "ppg_adjoint_vals_grad", "ppg_apply_poly_noalloc",
     "ppg_solve_batched", "ppg_build_poly_composite", "ppg_solve_double", "ppg_solve_chpoly",
-    "ppg_build_poly_checked",
+    "ppg_build_poly_checked", "ppg_sweep_plan_create", "ppg_sweep_plan_info",
+    "ppg_sweep_plan_destroy", "ppg_apply_poly_sweep", "ppg_solve_flex_sweep",
 )
 
 

@@ -12,7 +12,8 @@ import numpy as np
 import torch
 
 from ._binding import (PPG_F32, PPG_F64, Roots, check, default_opts, lib, ppg_roots,
-                       ppg_csr, ppg_poly_check, ppg_stats, csr_validate_host, _dp)
+                       ppg_csr, ppg_poly_check, ppg_stats, ppg_sweep_info, csr_validate_host,
+                       _dp)
 
 
 def _stream(stream=None):
@@ -165,13 +166,14 @@ def spmv(A: CSR, x: torch.Tensor, out: Optional[torch.Tensor] = None, stream=Non
 def solve(A: CSR, b: torch.Tensor, m: int = 50, tol: float = 1e-10,
           roots: Optional[Roots] = None, x0: Optional[torch.Tensor] = None,
           max_cycles: int = 10000, timing: bool = False, out: Optional[torch.Tensor] = None,
-          stream=None) -> Tuple[torch.Tensor, dict]:
+          stream=None, cgs2_fused: bool = False) -> Tuple[torch.Tensor, dict]:
     """PP-GMRES(m) (roots given) or GMRES(m); returns (x, stats)."""
     _need_cuda(b)
     x = torch.empty_like(b) if out is None else out
     if x0 is not None:
         x.copy_(x0)
-    o = default_opts(max_cycles=max_cycles, timing=int(timing), x0_given=int(x0 is not None))
+    o = default_opts(max_cycles=max_cycles, timing=int(timing), x0_given=int(x0 is not None),
+                     cgs2_fused=int(bool(cgs2_fused)))
     st = ppg_stats()
     rc = lib.ppg_solve(A.ref(), roots.ref() if roots is not None else None, _ptr(b), _ptr(x),
                        m, tol, C.byref(o), C.byref(st), _stream(stream))
@@ -192,6 +194,69 @@ def solve_flex(A64: CSR, A32: CSR, b: torch.Tensor, roots: Roots, m: int = 50,
     rc = lib.ppg_solve_flex(A64.ref(), A32.ref(), roots.ref(), _ptr(b), _ptr(x), m, tol,
                             C.byref(o), C.byref(st), _stream(stream))
     check(rc, "ppg_solve_flex")
+    s = st.as_dict()
+    s["status"] = rc
+    return x, s
+
+
+class SweepPlan:
+    """Multi-root fused sweep plan of an FP32 CSR (ppg_sweep_plan_create):
+    the matrix reordered into compact tiles of ``tile_rows`` rows (by
+    ``perm``, new -> old, or breadth-first growth when None), with each
+    tile's halo, so that a conjugate pair of Algorithm 3 runs in one pass."""
+
+    def __init__(self, A32: "CSR", tile_rows: int = 4096, perm=None, fuse: bool = True,
+                 stream=None):
+        if A32.dtype != PPG_F32:
+            raise ValueError("the sweep plan takes the FP32 matrix")
+        self._h = C.c_void_p()
+        pp = None
+        if perm is not None:
+            self._perm = np.ascontiguousarray(perm, dtype=np.int32)
+            pp = self._perm.ctypes.data_as(C.c_void_p)
+        check(lib.ppg_sweep_plan_create(A32.ref(), pp, int(tile_rows), int(bool(fuse)),
+                                        C.byref(self._h), _stream(stream)),
+              "ppg_sweep_plan_create")
+        self.n = A32.n
+
+    def info(self) -> dict:
+        i = ppg_sweep_info()
+        check(lib.ppg_sweep_plan_info(self._h, C.byref(i)), "ppg_sweep_plan_info")
+        return i.as_dict()
+
+    def apply_poly(self, roots: Roots, v: torch.Tensor, out: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+        _need_cuda(v)
+        if v.dtype != torch.float32:
+            raise ValueError("v must be float32")
+        y = torch.empty_like(v) if out is None else out
+        check(lib.ppg_apply_poly_sweep(self._h, roots.ref(), _ptr(v), _ptr(y),
+                                       _stream(stream)), "ppg_apply_poly_sweep")
+        return y
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.ppg_sweep_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_flex_sweep(A64: "CSR", plan: SweepPlan, b: torch.Tensor, roots: Roots,
+                     m: int = 50, tol: float = 1e-10, max_cycles: int = 10000,
+                     timing: bool = False, out: Optional[torch.Tensor] = None, stream=None):
+    """The precision form with p(A) v_j through a fused-sweep plan."""
+    _need_cuda(b)
+    x = torch.empty_like(b) if out is None else out
+    o = default_opts(max_cycles=max_cycles, timing=int(timing))
+    st = ppg_stats()
+    rc = lib.ppg_solve_flex_sweep(A64.ref(), plan._h, roots.ref(), _ptr(b), _ptr(x), m, tol,
+                                  C.byref(o), C.byref(st), _stream(stream))
+    check(rc, "ppg_solve_flex_sweep")
     s = st.as_dict()
     s["status"] = rc
     return x, s

@@ -310,6 +310,8 @@ struct SolveCore {
     float* fb = nullptr;
     float* fc = nullptr;
     float* v32 = nullptr;
+    float* zh = nullptr;                    // sweep form: p(A) v_j in the plan's ordering
+    const ppg_sweep_plan* sweep = nullptr;  // flexible form through a fused-sweep plan
     double* spart = nullptr;
     OrthoWs ows{};
     GmresState gs{};
@@ -318,13 +320,13 @@ struct SolveCore {
 };
 
 // CGS2 of basis column j + 1 (w) against columns 0..j: h1 = V^T w; w -= V h1;
-// h2 = V^T w; w -= V h2 with ||w||^2.  The middle two passes run fused (one
-// pass over V) when the basis layout allows it.
+// h2 = V^T w; w -= V h2 with ||w||^2.  With opts.cgs2_fused the middle two
+// passes run as one pass over V when the basis layout allows it.
 static int32_t cgs2_column(SolveCore& c, int j, double* w, bool with_self, EventPair* ev) {
     const int32_t n = c.A64->n;
     if (ev) ev->start(c.s);
     PPG_TRY(launch_cgs_dot(c.V, c.ldv, j + 1, w, n, with_self, c.ows.h1, c.ows, c.s));
-    if (cgs_fused_ok(c.V, c.ldv, j + 1, w)) {
+    if (c.opts.cgs2_fused && cgs_fused_ok(c.V, c.ldv, j + 1, w)) {
         PPG_TRY(launch_cgs_sub_dot(c.V, c.ldv, j + 1, w, n, c.ows.h1, c.ows.h2, c.ows, c.s));
     } else {
         PPG_TRY(launch_cgs_update(c.V, c.ldv, j + 1, w, n, c.ows.h1, false, nullptr, c.ows,
@@ -353,6 +355,7 @@ static int32_t build_core(const ppg_csr* A, int d, const double* v0, const ppg_o
     SolveCore c{};
     c.A64 = A;
     c.s = s;
+    c.opts = o;
     c.ldv = pad_ld(n);
     Arena ar;
     ar.add(&c.V, (size_t)c.ldv * (d + 1));
@@ -456,6 +459,7 @@ static int32_t run_solve(SolveCore& c) {
         ar.add(&c.fb, (size_t)n);
         ar.add(&c.fc, (size_t)n);
         ar.add(&c.v32, (size_t)n);
+        if (c.sweep) ar.add(&c.zh, (size_t)n);
     }
     ar.add(&c.va, (size_t)n);
     ar.add(&c.vb, (size_t)n);
@@ -572,8 +576,23 @@ static int32_t run_solve(SolveCore& c) {
     // update does not read.
     constexpr int kLookahead = 2;
     const std::vector<Step>* chain = pp ? (c.flex ? &c.p_plan : &c.phi_plan) : nullptr;
-    const int nahead = chain ? std::max(0, std::min(kLookahead, (int)chain->size() - 1)) : 0;
+    // (the fused-sweep chain runs whole: its pairs must not be split)
+    const int nahead = (chain && !c.sweep)
+                           ? std::max(0, std::min(kLookahead, (int)chain->size() - 1))
+                           : 0;
     auto chain_steps = [&](int j, int i0, int i1, double* by) -> int32_t {
+        if (c.sweep) {
+            Buffers fb{};
+            fb.ptr[B_IN] = c.v32;
+            fb.ptr[B_P] = c.zh;
+            fb.ptr[B_A] = c.fa;
+            fb.ptr[B_B] = c.fb;
+            fb.ptr[B_C] = c.fc;
+            if (i0 != 0 || i1 != (int)c.p_plan.size()) return PPG_ERR_ARG;
+            PPG_TRY(sweep_run_chain(c.sweep, c.p_plan, fb, s));
+            if (by) *by = sweep_chain_bytes(c.sweep, c.p_plan);
+            return sweep_scatter(c.sweep, c.zh, c.Z32 + (size_t)j * c.ldv, s);
+        }
         if (c.flex) {
             Buffers fb{};
             fb.ptr[B_IN] = c.v32;
@@ -593,7 +612,11 @@ static int32_t run_solve(SolveCore& c) {
     // (root steps only, not the cast) and chain steps [0, upto)
     auto begin_step = [&](int j, int e, int upto, double* by) -> int32_t {
         *by = 0.0;
-        if (c.flex) PPG_TRY(launch_cast_f64_f32(c.V + (size_t)j * c.ldv, c.v32, n, s));
+        if (c.sweep) {
+            PPG_TRY(sweep_gather(c.sweep, c.V + (size_t)j * c.ldv, true, c.v32, s));
+        } else if (c.flex) {
+            PPG_TRY(launch_cast_f64_f32(c.V + (size_t)j * c.ldv, c.v32, n, s));
+        }
         ev_poly[e].start(s);
         if (chain && upto > 0) PPG_TRY(chain_steps(j, 0, upto, by));
         return PPG_OK;
@@ -669,7 +692,9 @@ static int32_t run_solve(SolveCore& c) {
             c.st.poly_ms += ev_poly[e].ms();
             c.st.ortho_ms += ev_orth[e].ms();
             c.st.poly_bytes += by_step;
-            c.st.poly_launches += chain ? (int64_t)chain->size() : (c.flex ? 0 : 1);
+            c.st.poly_launches += chain ? (c.sweep ? sweep_chain_launches(c.sweep, *chain)
+                                                   : (int64_t)chain->size())
+                                        : (c.flex ? 0 : 1);
             c.st.mvps += pp ? d : 1;   // flexible form: d-1 in p(A) v_j, one for A z_j
             c.st.iters += 1;
             c.st.dots += 2 * (j + 1) + 1;
@@ -1021,7 +1046,7 @@ void ppg_default_opts(ppg_opts* o) {
     o->timing = 0;
     o->x0_given = 0;
     o->batch_mode = 0;
-    o->pad_ = 0;
+    o->cgs2_fused = 0;
     o->wait_timeout_ms = 5000.0;
 }
 
@@ -1191,6 +1216,31 @@ int32_t ppg_solve_flex(const ppg_csr* A64, const ppg_csr* A32, const ppg_roots* 
     SolveCore c{};
     c.A64 = A64;
     c.A32 = A32;
+    c.roots = r;
+    c.b = b;
+    c.x = x;
+    c.m = m;
+    c.tol = tol;
+    ppg_default_opts(&c.opts);
+    if (opts) c.opts = *opts;
+    c.flex = true;
+    c.s = (cudaStream_t)stream;
+    int32_t rc = run_solve(c);
+    if (stats) *stats = c.st;
+    return rc;
+}
+
+int32_t ppg_solve_flex_sweep(const ppg_csr* A64, const ppg_sweep_plan* plan, const ppg_roots* r,
+                             const double* b, double* x, int32_t m, double tol,
+                             const ppg_opts* opts, ppg_stats* stats, void* stream) {
+    PPG_TRY(check_csr(A64, PPG_F64));
+    PPG_TRY(check_roots(r));
+    if (!plan || sweep_plan_n(plan) != A64->n) return PPG_ERR_ARG;
+    if (!b || !x || b == x || m < 1 || m + 1 > ORTHO_MAXC || !(tol > 0.0)) return PPG_ERR_ARG;
+    SolveCore c{};
+    c.A64 = A64;
+    c.A32 = nullptr;
+    c.sweep = plan;
     c.roots = r;
     c.b = b;
     c.x = x;

@@ -199,6 +199,23 @@ int32_t run_plan(const std::vector<Step>& plan, const int32_t* rowptr,
                  bool reserve_l2 = true);
 
 // ---------------------------------------------------------------------------
+// Multi-root fused sweep (sweep.cu): Algorithm 3 on a plan's reordered FP32
+// matrix with each conjugate pair in one pass
+// ---------------------------------------------------------------------------
+
+int32_t sweep_run_chain(const ppg_sweep_plan* P, const std::vector<Step>& plan,
+                        const Buffers& bufs, cudaStream_t s);
+// y = x[perm] (x FP64 when x_f64, else FP32), into the plan's ordering
+int32_t sweep_gather(const ppg_sweep_plan* P, const void* x, bool x_f64, float* y,
+                     cudaStream_t s);
+// y[perm] = x, back to the original ordering
+int32_t sweep_scatter(const ppg_sweep_plan* P, const float* x, float* y, cudaStream_t s);
+// algorithmic bytes and launches of a chain run by sweep_run_chain
+double sweep_chain_bytes(const ppg_sweep_plan* P, const std::vector<Step>& plan);
+int64_t sweep_chain_launches(const ppg_sweep_plan* P, const std::vector<Step>& plan);
+int32_t sweep_plan_n(const ppg_sweep_plan* P);
+
+// ---------------------------------------------------------------------------
 // Orthogonalisation and small dense kernels
 // ---------------------------------------------------------------------------
 

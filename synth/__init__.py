@@ -128,6 +128,36 @@ def cd3d(N: int, beta_h: Tuple[float, float, float]) -> CSRHost:
     return _assemble(n, (-NN, -N, -1, 0, 1, N, NN), coeffs, valid)
 
 
+def block_order(dims: Tuple[int, ...], block: Tuple[int, ...]) -> np.ndarray:
+    """Row ordering of a lexicographic grid (x fastest) by blocks: the
+    blocks of ``block`` nodes (the last ones clipped) in lexicographic block
+    order, the nodes of a block lexicographic inside it.  Returns perm with
+    perm[new] = old (grid structure of the inputs; no arithmetic of the
+    method)."""
+    dims = tuple(int(d) for d in dims)
+    block = tuple(int(b) for b in block)
+    grids = np.meshgrid(*[np.arange(d) for d in reversed(dims)], indexing="ij")
+    # coordinates per old index (lexicographic, x fastest): reversed dims
+    coords = [g.ravel() for g in reversed(grids)]
+    old = np.zeros_like(coords[0])
+    stride = 1
+    for c, d in zip(coords, dims):
+        old = old + c * stride
+        stride *= d
+    bkey = np.zeros_like(old)
+    inkey = np.zeros_like(old)
+    bstride = 1
+    istride = 1
+    for c, d, b in zip(coords, dims, block):
+        nb = -(-d // b)
+        bkey = bkey + (c // b) * bstride
+        bstride *= nb
+        inkey = inkey + (c % b) * istride
+        istride *= b
+    key = bkey * istride + inkey
+    return old[np.argsort(key, kind="stable")].astype(np.int32)
+
+
 def diag_csr(d: np.ndarray) -> CSRHost:
     """Diagonal matrix diag(d) in CSR."""
     d = np.asarray(d, dtype=np.float64)

@@ -59,6 +59,14 @@ def test_cd2d_200_iteration_parity(env):
     assert rel <= P.tol
     assert abs(st["true_relres"] - rel) <= 1e-3 * rel
     assert np.linalg.norm(xg - xo) <= 1e-6 * np.linalg.norm(xo)
+    # CGS2 with its middle passes fused (one pass over the basis, the same
+    # multiply-adds in another order): the same solve within the same bounds
+    xf, sf = p.solve(A, to_dev(torch, P.b), P.m, P.tol, roots=R, cgs2_fused=True)
+    assert sf["converged"] == 1 and abs(sf["iters"] - so.iters) <= 2
+    assert sf["cycles"] == so.cycles
+    xfg = xf.cpu().numpy()
+    assert np.linalg.norm(P.b - As @ xfg) / np.linalg.norm(P.b) <= P.tol
+    assert np.linalg.norm(xfg - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
 @pytest.mark.parametrize("inner", ["f32", "f64"])
