@@ -581,6 +581,15 @@ def measure_forms(device):
         return {"chains": what, "achieved_gbs": round(gbs, 1),
                 "frac": round(gbs / hbm, 4), "peak_gbs": hbm,
                 "launches": st["poly_launches"], "ms": round(st["poly_ms"], 2)}
+    # the same FP32-inner solve with every conjugate pair of Algorithm 3 in
+    # one pass (multi-root fused sweep over 16^3 blocks of the grid)
+    plan = ppg.SweepPlan(A32, 4096, perm=synth.block_order((160, 160, 160), (16, 16, 16)))
+    ppg.solve_flex_sweep(A64, plan, b, R, P.m, P.tol)
+    (xsw, ssw), tsw = _timed(torch, lambda: ppg.solve_flex_sweep(A64, plan, b, R, P.m, P.tol))
+    _, swt = ppg.solve_flex_sweep(A64, plan, b, R, P.m, P.tol, timing=True)
+    sweep_same = bool(torch.equal(xsw, x32))
+    sweep_info = plan.info()
+    plan.close()
     As = P.A.to_scipy()
     xh32, xh64 = x32.cpu().numpy(), x64.cpu().numpy()
     out["precision_cd3d_160"] = {
@@ -592,6 +601,17 @@ def measure_forms(device):
         "fp64_ms": round(t64, 2), "fp64_iters": s64["iters"],
         "fp64_relres": float(np.linalg.norm(P.b - As @ xh64) / np.linalg.norm(P.b)),
         "rel_diff_fp32_vs_fp64": float(np.linalg.norm(xh32 - xh64) / np.linalg.norm(xh64)),
+        "sweep": {"what": "FP32-inner FGMRES(50) with each conjugate pair of Algorithm 3 in one "
+                          "pass (16^3-block tiles of 4096 rows and their halos)",
+                  "solve_ms": round(tsw, 2), "iters": ssw["iters"],
+                  "identical_to_unfused": sweep_same,
+                  "chains_ms": round(swt["poly_ms"], 2),
+                  "chains_ms_unfused": round(f32t["poly_ms"], 2),
+                  "chain_launches": swt["poly_launches"],
+                  "chain_launches_unfused": f32t["poly_launches"],
+                  "chain_roofline": chain_bw(swt, "fused-sweep chains (Algorithm 3, FP32)"),
+                  "halo_fraction": round(sweep_info["halo_fraction"], 4),
+                  "ntiles": sweep_info["ntiles"]},
     }
     out["spmv_yardstick"] = spmv_yardstick(device, A64, A32, P.A.n)
     del A64, A32, x32, x64
@@ -604,6 +624,12 @@ def measure_forms(device):
     with torch.cuda.stream(side):
         ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10)
         (Xs, info), tb = _timed(torch, lambda: ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10))
+        # the same call with one CUDA graph per restart cycle instead of the
+        # persistent launch
+        ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10, persistent=False)
+        (Xg, infog), tg = _timed(torch, lambda: ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10,
+                                                                  persistent=False))
+    graph_same = all(torch.equal(a, b) for a, b in zip(Xs, Xg))
     worst = max(float(np.linalg.norm(B[k] - A.to_scipy() @ Xs[s][k].cpu().numpy())
                       / np.linalg.norm(B[k]))
                 for s, (A, B, _) in enumerate(probs) for k in range(4))
@@ -619,7 +645,9 @@ def measure_forms(device):
         seq_ms += t
     out["batched_64x4"] = {
         "solves": 256, "total_rows": int(sum(A.n for A, _, _ in probs)),
-        "batched_ms": round(tb, 2), "worst_true_relres": worst,
+        "batched_ms": round(tb, 2), "launch": "one persistent cooperative kernel for the solve",
+        "graph_per_cycle_ms": round(tg, 2), "graph_per_cycle_identical": graph_same,
+        "worst_true_relres": worst,
         "cycles": info["stats"]["cycles"], "total_iters": info["stats"]["iters"],
         "fp64_sequential_ms_extrapolated": round(seq_ms / len(sample) * 64, 1),
         "fp64_sequential_sample": "8 of 64 systems (every 8th), 4 rhs each, one at a time",
