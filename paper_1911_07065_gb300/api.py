@@ -207,7 +207,7 @@ class SweepPlan:
 
     def __init__(self, A32: "CSR", tile_rows: int = 4096, perm=None, fuse: bool = True,
                  stream=None):
-        if A32.dtype != PPG_F32:
+        if A32.dtype != torch.float32:
             raise ValueError("the sweep plan takes the FP32 matrix")
         self._h = C.c_void_p()
         pp = None
