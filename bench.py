@@ -204,17 +204,36 @@ def oracle_c1():
             "true_relres": float(np.linalg.norm(P.b - As @ x) / np.linalg.norm(P.b))}
 
 
+def oracle_precision_small(out_path):
+    """The oracle's FP64 PP-GMRES(50) on the 40^3 version of the precision
+    workload (same seed and recipe; the device roots are rebuilt by the
+    oracle from the same v0), its solution saved to out_path (.npy)."""
+    import numpy as np
+    import synth
+    from oracle import gmres, poly
+
+    P = synth.problem("cd3d_160", scale=40)
+    As = P.A.to_scipy()
+    t0 = time.perf_counter()
+    pp = poly.build_poly(As, P.d, P.v0)
+    x, st = gmres.pp_gmres(As, pp.roots, P.b, P.m, P.tol)
+    t = time.perf_counter() - t0
+    np.save(out_path, x)
+    return {"solve_ms": 1e3 * t, "iters": st.iters,
+            "true_relres": float(np.linalg.norm(P.b - As @ x) / np.linalg.norm(P.b))}
+
+
 def _oracle_cores():
     return os.cpu_count() or 1
 
 
-def _run_oracle_subprocess(n_iters, mode="--oracle-sample"):
+def _run_oracle_subprocess(arg, mode="--oracle-sample"):
     """Run the oracle in a child process with BLAS threads on all host cores
     (SciPy's sparse matvec itself is single-threaded)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(_oracle_cores())
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), mode, str(n_iters)],
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), mode, str(arg)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -429,7 +448,7 @@ def run_ours(args, rank, local, world):
         "plain_gmres50": plain,
     }
     if rank == 0 and not args.no_forms:
-        line["forms"] = measure_forms(device)
+        line["forms"] = measure_forms(device, with_oracle=not args.no_cpu_baseline)
     if rank == 0 and not args.no_cpu_baseline:
         s = _run_oracle_subprocess(args.oracle_iters)
         v = _extrapolate(s, st["iters"], st["cycles"])
@@ -568,7 +587,39 @@ def measure_c1(device):
                        "cores": _oracle_cores(), "kind": "oracle, full solve (build + PP-GMRES)"}}
 
 
-def measure_forms(device):
+def precision_vs_oracle(device):
+    """The precision form's error against the FP64 oracle where the oracle
+    runs the whole solve: the 40^3 version of the precision workload (same
+    seeds and recipe, d = 60, FGMRES(50), tol 1e-10), the oracle's own FP64
+    PP-GMRES solution (its CPU run, timed) against the device's FP32-inner
+    and FP64 solutions."""
+    import numpy as np
+    import torch
+
+    import paper_1911_07065_gb300 as ppg
+    import synth
+
+    P = synth.problem("cd3d_160", scale=40)
+    A64 = ppg.CSR.from_host(P.A.rowptr, P.A.colind, P.A.vals, device=device)
+    A32 = A64.astype(torch.float32)
+    b = torch.from_numpy(P.b).to(device)
+    R = ppg.build_poly(A64, P.d, torch.from_numpy(P.v0).to(device))
+    x32, s32 = ppg.solve_flex(A64, A32, b, R, P.m, P.tol)
+    x64, s64 = ppg.solve(A64, b, P.m, P.tol, roots=R)
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    orc = _run_oracle_subprocess(path, "--oracle-precision-small")
+    xo = np.load(path)
+    os.unlink(path)
+    nx = np.linalg.norm(xo)
+    return {"n": P.A.n, "oracle_fp64_ms": round(orc["solve_ms"], 1),
+            "oracle_iters": orc["iters"], "oracle_cores": _oracle_cores(),
+            "fp32_inner_iters": s32["iters"], "fp64_iters": s64["iters"],
+            "err_fp32_inner_vs_oracle": float(np.linalg.norm(x32.cpu().numpy() - xo) / nx),
+            "err_fp64_vs_oracle": float(np.linalg.norm(x64.cpu().numpy() - xo) / nx)}
+
+
+def measure_forms(device, with_oracle=True):
     """The three forms beside the plain FP64 method, each against the plain
     FP64 PP-GMRES on the same GPU at relative residual 1e-10 (one run each,
     after one warm-up run)."""
@@ -644,6 +695,8 @@ def measure_forms(device):
                   "ntiles": sweep_info["ntiles"]},
     }
     out["spmv_yardstick"] = spmv_yardstick(device, A64, A32, P.A.n)
+    if with_oracle:
+        out["precision_cd3d_40_vs_oracle"] = precision_vs_oracle(device)
     del A64, A32, x32, x64
     # batching form: 64 systems x 4 right-hand sides in one call
     probs = synth.batch_problem(nsys=64, seed=104)
@@ -810,6 +863,7 @@ def main():
     ap.add_argument("--ref-cycles", type=int, default=4)
     ap.add_argument("--oracle-sample", type=int, default=None)
     ap.add_argument("--oracle-c1", type=int, default=None)
+    ap.add_argument("--oracle-precision-small", default=None)
     ap.add_argument("--profile-case", default=None)
     args = ap.parse_args()
     if args.profile_case:
@@ -819,6 +873,9 @@ def main():
         return 0
     if args.oracle_c1 is not None:
         print(json.dumps(oracle_c1()))
+        return 0
+    if args.oracle_precision_small is not None:
+        print(json.dumps(oracle_precision_small(args.oracle_precision_small)))
         return 0
     rank, local, world = _dist_env()
     if args.impl == "reference":
