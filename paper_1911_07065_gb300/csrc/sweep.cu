@@ -40,12 +40,14 @@ struct ppg_sweep_plan {
 namespace ppg {
 namespace {
 
-constexpr int SW_THREADS = 512;
+constexpr int SW_THREADS = 1024;   // one CTA per SM; a thread owns one row of a sub-tile
+constexpr int SW_CHUNK = 8192;     // nonzeros staged per chunk (64 KB)
 
-// Largest halo a tile may have for its tmp values to fit in shared memory
-// with the tile's (T + halo) tmp values, T p' values and the halo list.
+// Shared memory of one tile: the staging chunk, tmp over the tile and its
+// halo, p' of the tile's rows, the halo list.
 size_t sweep_smem(int T, int halo) {
-    return (size_t)(T + halo) * sizeof(float) + (size_t)T * sizeof(float) +
+    return (size_t)SW_CHUNK * (sizeof(float) + sizeof(int32_t)) +
+           (size_t)(T + halo) * sizeof(float) + (size_t)T * sizeof(float) +
            (size_t)halo * sizeof(int32_t);
 }
 
@@ -58,11 +60,26 @@ __device__ __forceinline__ int halo_slot(const int32_t* h, int nh, int32_t c) {
     return lo;
 }
 
+__device__ __forceinline__ void sw_stage(float* sval, int32_t* scol, const float* vals,
+                                         const int32_t* colind, int32_t c0, int32_t c1) {
+    for (int32_t k = c0 + threadIdx.x; k < c1; k += SW_THREADS) {
+        const unsigned sv = (unsigned)__cvta_generic_to_shared(sval + (k - c0));
+        const unsigned sc = (unsigned)__cvta_generic_to_shared(scol + (k - c0));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sv), "l"(vals + k) : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sc), "l"(colind + k)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // One conjugate pair over one tile (see the file comment).  prod = a0 of
 // both steps, p = the accumulator (a1 of P_PAIR1, read unless PZERO),
 // pout = o0 of P_PAIR1 (p'), qout = o0 of P_PAIR2 (prod', or p'' when
-// FINAL: qout = pout then).
-__global__ void __launch_bounds__(SW_THREADS)
+// FINAL: qout = pout then).  The tile's rows go in sub-tiles of SW_THREADS
+// rows whose nonzeros are staged in shared memory by coalesced copies (in
+// chunks, so any row length works); each row sums its products in stored
+// order, as the unfused kernel does.
+__global__ void __launch_bounds__(SW_THREADS, 1)
 k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
              const float* __restrict__ vals, int32_t n, int T,
              const int32_t* __restrict__ halo_off, const int32_t* __restrict__ halo_idx,
@@ -73,48 +90,102 @@ k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col
     const int32_t lo = tile * T;
     const int rows = min(T, n - lo);
     const int h0 = halo_off[tile], nh = halo_off[tile + 1] - h0;
-    float* tmp_s = reinterpret_cast<float*>(sw_raw);   // [T + nh]
-    float* pp_s = tmp_s + T + nh;                       // [T]
+    float* sval = reinterpret_cast<float*>(sw_raw);
+    int32_t* scol = reinterpret_cast<int32_t*>(sval + SW_CHUNK);
+    float* tmp_s = reinterpret_cast<float*>(scol + SW_CHUNK);   // [T + nh]
+    float* pp_s = tmp_s + T + nh;                                // [T]
     int32_t* halo_s = reinterpret_cast<int32_t*>(pp_s + T);
     const int tid = threadIdx.x;
     for (int i = tid; i < nh; i += SW_THREADS) halo_s[i] = halo_idx[h0 + i];
-    __syncthreads();
-    // phase A: tmp = c1 prod - A prod over the tile and its halo; p' for the tile
-    for (int li = tid; li < rows + nh; li += SW_THREADS) {
-        const int32_t g = li < rows ? lo + li : halo_s[li - rows];
+
+    // phase A, tile rows: tmp = c1 prod - A prod; p'
+    for (int sub = 0; sub < rows; sub += SW_THREADS) {
+        const int32_t r0 = lo + sub;
+        const int nr = min(SW_THREADS, rows - sub);
+        const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
+        const bool mine = tid < nr;
+        const int32_t g = r0 + tid;
+        const int32_t rlo = mine ? __ldg(rowptr + g) : k1;
+        const int32_t rhi = mine ? __ldg(rowptr + g + 1) : k1;
         float acc = 0.f;
-        for (int32_t k = __ldg(rowptr + g), e = __ldg(rowptr + g + 1); k < e; ++k)
-            acc = fmaf(__ldg(vals + k), __ldg(prod + __ldg(colind + k)), acc);
-        const float tmp = fmaf(c1, __ldg(prod + g), -acc);
-        if (li < rows) {
-            tmp_s[li] = tmp;
+        for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
+            const int32_t cend = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, cend);
+            __syncthreads();
+            int32_t k = max(rlo, c0) - c0;
+            const int32_t hi = min(rhi, cend) - c0;
+            for (; k + 4 <= hi; k += 4) {   // four gathers in flight, sums in order
+                const float x0 = __ldg(prod + scol[k]), x1 = __ldg(prod + scol[k + 1]);
+                const float x2 = __ldg(prod + scol[k + 2]), x3 = __ldg(prod + scol[k + 3]);
+                acc = fmaf(sval[k], x0, acc);
+                acc = fmaf(sval[k + 1], x1, acc);
+                acc = fmaf(sval[k + 2], x2, acc);
+                acc = fmaf(sval[k + 3], x3, acc);
+            }
+            for (; k < hi; ++k) acc = fmaf(sval[k], __ldg(prod + scol[k]), acc);
+            __syncthreads();
+        }
+        if (mine) {
+            const float tmp = fmaf(c1, __ldg(prod + g), -acc);
+            tmp_s[sub + tid] = tmp;
             const float pn = pzero ? c2 * tmp : fmaf(c2, tmp, p[g]);
             if (final_) {
-                pp_s[li] = pn;
+                pp_s[sub + tid] = pn;
             } else {
                 pout[g] = pn;
             }
-        } else {
-            tmp_s[T + (li - rows)] = tmp;
         }
+    }
+    // phase A, halo rows: the same tmp, one row per thread from global memory
+    for (int li = tid; li < nh; li += SW_THREADS) {
+        const int32_t g = halo_s[li];
+        float acc = 0.f;
+        int32_t k = __ldg(rowptr + g);
+        const int32_t e = __ldg(rowptr + g + 1);
+        for (; k + 4 <= e; k += 4) {
+            const float x0 = __ldg(prod + __ldg(colind + k)), x1 = __ldg(prod + __ldg(colind + k + 1));
+            const float x2 = __ldg(prod + __ldg(colind + k + 2)), x3 = __ldg(prod + __ldg(colind + k + 3));
+            acc = fmaf(__ldg(vals + k), x0, acc);
+            acc = fmaf(__ldg(vals + k + 1), x1, acc);
+            acc = fmaf(__ldg(vals + k + 2), x2, acc);
+            acc = fmaf(__ldg(vals + k + 3), x3, acc);
+        }
+        for (; k < e; ++k) acc = fmaf(__ldg(vals + k), __ldg(prod + __ldg(colind + k)), acc);
+        tmp_s[T + li] = fmaf(c1, __ldg(prod + g), -acc);
     }
     __syncthreads();
     // phase B: prod' = prod - c2 A tmp for the tile's rows, tmp from shared
-    // memory (tile columns by offset, halo columns by binary search)
-    for (int li = tid; li < rows; li += SW_THREADS) {
-        const int32_t g = lo + li;
+    // memory (tile columns by offset, halo columns by binary search); the
+    // tile's nonzeros are staged again (from L2: this CTA read them just now)
+    for (int sub = 0; sub < rows; sub += SW_THREADS) {
+        const int32_t r0 = lo + sub;
+        const int nr = min(SW_THREADS, rows - sub);
+        const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
+        const bool mine = tid < nr;
+        const int32_t g = r0 + tid;
+        const int32_t rlo = mine ? __ldg(rowptr + g) : k1;
+        const int32_t rhi = mine ? __ldg(rowptr + g + 1) : k1;
         float acc = 0.f;
-        for (int32_t k = __ldg(rowptr + g), e = __ldg(rowptr + g + 1); k < e; ++k) {
-            const int32_t c = __ldg(colind + k);
-            const float t = (c >= lo && c < lo + rows) ? tmp_s[c - lo]
-                                                       : tmp_s[T + halo_slot(halo_s, nh, c)];
-            acc = fmaf(__ldg(vals + k), t, acc);
+        for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
+            const int32_t cend = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, cend);
+            __syncthreads();
+            const int32_t hi = min(rhi, cend) - c0;
+            for (int32_t k = max(rlo, c0) - c0; k < hi; ++k) {
+                const int32_t c = scol[k];
+                const float t = (c >= lo && c < lo + rows) ? tmp_s[c - lo]
+                                                           : tmp_s[T + halo_slot(halo_s, nh, c)];
+                acc = fmaf(sval[k], t, acc);
+            }
+            __syncthreads();
         }
-        const float prodn = fmaf(-c2, acc, __ldg(prod + g));
-        if (final_) {
-            qout[g] = fmaf(c3, prodn, pp_s[li]);
-        } else {
-            qout[g] = prodn;
+        if (mine) {
+            const float prodn = fmaf(-c2, acc, __ldg(prod + g));
+            if (final_) {
+                qout[g] = fmaf(c3, prodn, pp_s[sub + tid]);
+            } else {
+                qout[g] = prodn;
+            }
         }
     }
 }
