@@ -40,15 +40,15 @@ struct ppg_sweep_plan {
 namespace ppg {
 namespace {
 
-constexpr int SW_THREADS = 1024;   // one CTA per SM; a thread owns one row of a sub-tile
-constexpr int SW_CHUNK = 8192;     // nonzeros staged per chunk (64 KB)
+constexpr int SW_THREADS = 256;    // threads per CTA; a thread owns two rows of a sub-tile
+constexpr int SW_SUB = 2 * SW_THREADS;   // rows per sub-tile
+constexpr int SW_CHUNK = 4096;     // nonzeros staged per chunk (32 KB)
 
 // Shared memory of one tile: the staging chunk, tmp over the tile and its
-// halo, p' of the tile's rows, the halo list.
+// halo, the halo list.
 size_t sweep_smem(int T, int halo) {
     return (size_t)SW_CHUNK * (sizeof(float) + sizeof(int32_t)) +
-           (size_t)(T + halo) * sizeof(float) + (size_t)T * sizeof(float) +
-           (size_t)halo * sizeof(int32_t);
+           (size_t)(T + halo) * sizeof(float) + (size_t)halo * sizeof(int32_t);
 }
 
 __device__ __forceinline__ int halo_slot(const int32_t* h, int nh, int32_t c) {
@@ -72,14 +72,34 @@ __device__ __forceinline__ void sw_stage(float* sval, int32_t* scol, const float
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// acc_a / acc_b += the staged products of rows a and b (staged ranges
+// [ka, ha) and [kb, hb)), both rows' gathers in flight together, each row
+// summed in stored order.  X(c) gives the vector entry of column c.
+template <typename XF>
+__device__ __forceinline__ void sw_two_rows(const float* sval, const int32_t* scol, int32_t ka,
+                                            int32_t ha, int32_t kb, int32_t hb, float& acc_a,
+                                            float& acc_b, XF X) {
+    for (; ka + 2 <= ha && kb + 2 <= hb; ka += 2, kb += 2) {
+        const float xa0 = X(scol[ka]), xa1 = X(scol[ka + 1]);
+        const float xb0 = X(scol[kb]), xb1 = X(scol[kb + 1]);
+        acc_a = fmaf(sval[ka], xa0, acc_a);
+        acc_a = fmaf(sval[ka + 1], xa1, acc_a);
+        acc_b = fmaf(sval[kb], xb0, acc_b);
+        acc_b = fmaf(sval[kb + 1], xb1, acc_b);
+    }
+    for (; ka < ha; ++ka) acc_a = fmaf(sval[ka], X(scol[ka]), acc_a);
+    for (; kb < hb; ++kb) acc_b = fmaf(sval[kb], X(scol[kb]), acc_b);
+}
+
 // One conjugate pair over one tile (see the file comment).  prod = a0 of
 // both steps, p = the accumulator (a1 of P_PAIR1, read unless PZERO),
 // pout = o0 of P_PAIR1 (p'), qout = o0 of P_PAIR2 (prod', or p'' when
-// FINAL: qout = pout then).  The tile's rows go in sub-tiles of SW_THREADS
-// rows whose nonzeros are staged in shared memory by coalesced copies (in
-// chunks, so any row length works); each row sums its products in stored
-// order, as the unfused kernel does.
-__global__ void __launch_bounds__(SW_THREADS, 1)
+// FINAL: qout = pout then, and p' goes through pout between the phases).
+// The tile's rows go in sub-tiles of SW_SUB rows, two per thread, whose
+// nonzeros are staged in shared memory by coalesced copies (in chunks, so
+// any row length works); each row sums its products in stored order, as
+// the unfused kernel does.
+__global__ void __launch_bounds__(SW_THREADS)
 k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
              const float* __restrict__ vals, int32_t n, int T,
              const int32_t* __restrict__ halo_off, const int32_t* __restrict__ halo_idx,
@@ -93,98 +113,94 @@ k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col
     float* sval = reinterpret_cast<float*>(sw_raw);
     int32_t* scol = reinterpret_cast<int32_t*>(sval + SW_CHUNK);
     float* tmp_s = reinterpret_cast<float*>(scol + SW_CHUNK);   // [T + nh]
-    float* pp_s = tmp_s + T + nh;                                // [T]
-    int32_t* halo_s = reinterpret_cast<int32_t*>(pp_s + T);
+    int32_t* halo_s = reinterpret_cast<int32_t*>(tmp_s + T + nh);
     const int tid = threadIdx.x;
     for (int i = tid; i < nh; i += SW_THREADS) halo_s[i] = halo_idx[h0 + i];
+    auto xprod = [&](int32_t c) { return __ldg(prod + c); };
 
     // phase A, tile rows: tmp = c1 prod - A prod; p'
-    for (int sub = 0; sub < rows; sub += SW_THREADS) {
+    for (int sub = 0; sub < rows; sub += SW_SUB) {
         const int32_t r0 = lo + sub;
-        const int nr = min(SW_THREADS, rows - sub);
+        const int nr = min(SW_SUB, rows - sub);
         const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
-        const bool mine = tid < nr;
-        const int32_t g = r0 + tid;
-        const int32_t rlo = mine ? __ldg(rowptr + g) : k1;
-        const int32_t rhi = mine ? __ldg(rowptr + g + 1) : k1;
-        float acc = 0.f;
+        const int ia = tid, ib = tid + SW_THREADS;
+        const int32_t alo = ia < nr ? __ldg(rowptr + r0 + ia) : k1;
+        const int32_t ahi = ia < nr ? __ldg(rowptr + r0 + ia + 1) : k1;
+        const int32_t blo = ib < nr ? __ldg(rowptr + r0 + ib) : k1;
+        const int32_t bhi = ib < nr ? __ldg(rowptr + r0 + ib + 1) : k1;
+        float acc_a = 0.f, acc_b = 0.f;
         for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
-            const int32_t cend = min(k1, c0 + SW_CHUNK);
-            sw_stage(sval, scol, vals, colind, c0, cend);
+            const int32_t ce = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, ce);
             __syncthreads();
-            int32_t k = max(rlo, c0) - c0;
-            const int32_t hi = min(rhi, cend) - c0;
-            for (; k + 4 <= hi; k += 4) {   // four gathers in flight, sums in order
-                const float x0 = __ldg(prod + scol[k]), x1 = __ldg(prod + scol[k + 1]);
-                const float x2 = __ldg(prod + scol[k + 2]), x3 = __ldg(prod + scol[k + 3]);
-                acc = fmaf(sval[k], x0, acc);
-                acc = fmaf(sval[k + 1], x1, acc);
-                acc = fmaf(sval[k + 2], x2, acc);
-                acc = fmaf(sval[k + 3], x3, acc);
-            }
-            for (; k < hi; ++k) acc = fmaf(sval[k], __ldg(prod + scol[k]), acc);
+            sw_two_rows(sval, scol, max(alo, c0) - c0, min(ahi, ce) - c0, max(blo, c0) - c0,
+                        min(bhi, ce) - c0, acc_a, acc_b, xprod);
             __syncthreads();
         }
-        if (mine) {
-            const float tmp = fmaf(c1, __ldg(prod + g), -acc);
-            tmp_s[sub + tid] = tmp;
-            const float pn = pzero ? c2 * tmp : fmaf(c2, tmp, p[g]);
-            if (final_) {
-                pp_s[sub + tid] = pn;
-            } else {
-                pout[g] = pn;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = q ? ib : ia;
+            if (i < nr) {
+                const int32_t g = r0 + i;
+                const float tmp = fmaf(c1, __ldg(prod + g), -(q ? acc_b : acc_a));
+                tmp_s[sub + i] = tmp;
+                pout[g] = pzero ? c2 * tmp : fmaf(c2, tmp, p[g]);
             }
         }
     }
-    // phase A, halo rows: the same tmp, one row per thread from global memory
-    for (int li = tid; li < nh; li += SW_THREADS) {
-        const int32_t g = halo_s[li];
-        float acc = 0.f;
-        int32_t k = __ldg(rowptr + g);
-        const int32_t e = __ldg(rowptr + g + 1);
-        for (; k + 4 <= e; k += 4) {
-            const float x0 = __ldg(prod + __ldg(colind + k)), x1 = __ldg(prod + __ldg(colind + k + 1));
-            const float x2 = __ldg(prod + __ldg(colind + k + 2)), x3 = __ldg(prod + __ldg(colind + k + 3));
-            acc = fmaf(__ldg(vals + k), x0, acc);
-            acc = fmaf(__ldg(vals + k + 1), x1, acc);
-            acc = fmaf(__ldg(vals + k + 2), x2, acc);
-            acc = fmaf(__ldg(vals + k + 3), x3, acc);
+    // phase A, halo rows: the same tmp, two rows per thread from global memory
+    for (int li = tid; li < nh; li += 2 * SW_THREADS) {
+        const int lj = li + SW_THREADS;
+        const int32_t ga = halo_s[li];
+        const int32_t gb = lj < nh ? halo_s[lj] : ga;
+        int32_t ka = __ldg(rowptr + ga), kb = __ldg(rowptr + gb);
+        const int32_t ea = __ldg(rowptr + ga + 1), eb = lj < nh ? __ldg(rowptr + gb + 1) : kb;
+        float acc_a = 0.f, acc_b = 0.f;
+        for (; ka + 2 <= ea && kb + 2 <= eb; ka += 2, kb += 2) {
+            const float xa0 = __ldg(prod + __ldg(colind + ka)), xa1 = __ldg(prod + __ldg(colind + ka + 1));
+            const float xb0 = __ldg(prod + __ldg(colind + kb)), xb1 = __ldg(prod + __ldg(colind + kb + 1));
+            acc_a = fmaf(__ldg(vals + ka), xa0, acc_a);
+            acc_a = fmaf(__ldg(vals + ka + 1), xa1, acc_a);
+            acc_b = fmaf(__ldg(vals + kb), xb0, acc_b);
+            acc_b = fmaf(__ldg(vals + kb + 1), xb1, acc_b);
         }
-        for (; k < e; ++k) acc = fmaf(__ldg(vals + k), __ldg(prod + __ldg(colind + k)), acc);
-        tmp_s[T + li] = fmaf(c1, __ldg(prod + g), -acc);
+        for (; ka < ea; ++ka) acc_a = fmaf(__ldg(vals + ka), __ldg(prod + __ldg(colind + ka)), acc_a);
+        for (; kb < eb; ++kb) acc_b = fmaf(__ldg(vals + kb), __ldg(prod + __ldg(colind + kb)), acc_b);
+        tmp_s[T + li] = fmaf(c1, __ldg(prod + ga), -acc_a);
+        if (lj < nh) tmp_s[T + lj] = fmaf(c1, __ldg(prod + gb), -acc_b);
     }
-    __syncthreads();
+    __syncthreads();   // tmp complete; p' of the tile written (read back below when FINAL)
     // phase B: prod' = prod - c2 A tmp for the tile's rows, tmp from shared
     // memory (tile columns by offset, halo columns by binary search); the
     // tile's nonzeros are staged again (from L2: this CTA read them just now)
-    for (int sub = 0; sub < rows; sub += SW_THREADS) {
+    auto xtmp = [&](int32_t c) {
+        return (c >= lo && c < lo + rows) ? tmp_s[c - lo] : tmp_s[T + halo_slot(halo_s, nh, c)];
+    };
+    for (int sub = 0; sub < rows; sub += SW_SUB) {
         const int32_t r0 = lo + sub;
-        const int nr = min(SW_THREADS, rows - sub);
+        const int nr = min(SW_SUB, rows - sub);
         const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
-        const bool mine = tid < nr;
-        const int32_t g = r0 + tid;
-        const int32_t rlo = mine ? __ldg(rowptr + g) : k1;
-        const int32_t rhi = mine ? __ldg(rowptr + g + 1) : k1;
-        float acc = 0.f;
+        const int ia = tid, ib = tid + SW_THREADS;
+        const int32_t alo = ia < nr ? __ldg(rowptr + r0 + ia) : k1;
+        const int32_t ahi = ia < nr ? __ldg(rowptr + r0 + ia + 1) : k1;
+        const int32_t blo = ib < nr ? __ldg(rowptr + r0 + ib) : k1;
+        const int32_t bhi = ib < nr ? __ldg(rowptr + r0 + ib + 1) : k1;
+        float acc_a = 0.f, acc_b = 0.f;
         for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
-            const int32_t cend = min(k1, c0 + SW_CHUNK);
-            sw_stage(sval, scol, vals, colind, c0, cend);
+            const int32_t ce = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, ce);
             __syncthreads();
-            const int32_t hi = min(rhi, cend) - c0;
-            for (int32_t k = max(rlo, c0) - c0; k < hi; ++k) {
-                const int32_t c = scol[k];
-                const float t = (c >= lo && c < lo + rows) ? tmp_s[c - lo]
-                                                           : tmp_s[T + halo_slot(halo_s, nh, c)];
-                acc = fmaf(sval[k], t, acc);
-            }
+            sw_two_rows(sval, scol, max(alo, c0) - c0, min(ahi, ce) - c0, max(blo, c0) - c0,
+                        min(bhi, ce) - c0, acc_a, acc_b, xtmp);
             __syncthreads();
         }
-        if (mine) {
-            const float prodn = fmaf(-c2, acc, __ldg(prod + g));
-            if (final_) {
-                qout[g] = fmaf(c3, prodn, pp_s[sub + tid]);
-            } else {
-                qout[g] = prodn;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = q ? ib : ia;
+            if (i < nr) {
+                const int32_t g = r0 + i;
+                const float prodn = fmaf(-c2, q ? acc_b : acc_a, __ldg(prod + g));
+                qout[g] = final_ ? fmaf(c3, prodn, pout[g]) : prodn;
             }
         }
     }
