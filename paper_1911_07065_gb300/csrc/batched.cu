@@ -87,56 +87,6 @@ __device__ __forceinline__ bool sys_live(const int32_t* active, int s) {
     return any != 0;
 }
 
-// The root update of one row of one step (the epilogue of a batched root
-// step), given acc = (A x)[r] for the NR right-hand sides and the row's
-// inputs e0 = a0[r], e1 = a1[r]; sq receives the squares of OP_RESID (set
-// for every op but the degree-one update, whose caller does not read it).
-template <typename T, int NR>
-__device__ __forceinline__ void bstep_row_epilogue(const BStep& st, int64_t r, const T (&acc)[NR],
-                                                   const T (&e0)[NR], const T (&e1)[NR],
-                                                   const BufSet<T>& b, const T* x,
-                                                   double (&sq)[NR]) {
-    const T c1 = (T)st.c1, c2 = (T)st.c2, c3 = (T)st.c3;
-    T* o0 = st.o0 >= 0 ? b.p[st.o0] + r * NR : nullptr;
-    if (st.op == OP_AXPY_B) {   // degree-one polynomial: P = c1 v (+ P)
-        T xr[NR];
-        ld_rhs<T, NR>(x + r * NR, xr);
-#pragma unroll
-        for (int i = 0; i < NR; ++i)
-            o0[i] = (st.flags & F_PZERO) ? c1 * xr[i] : fma(c1, xr[i], e1[i]);
-        return;
-    }
-    T* o1 = st.o1 >= 0 ? b.p[st.o1] + r * NR : nullptr;
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        sq[i] = 0.0;
-        const T s_ = acc[i];
-        if (st.op == OP_SPMV) {
-            o0[i] = s_;
-        } else if (st.op == OP_RESID) {
-            const T v = e0[i] - s_;
-            o0[i] = v;
-            sq[i] = (double)v * (double)v;
-        } else if (st.op == OP_P_REAL) {
-            const T pnew = (st.flags & F_PZERO) ? c1 * e0[i] : fma(c1, e0[i], e1[i]);
-            const T prodn = fma(-c1, s_, e0[i]);
-            if (st.flags & F_FINAL) {
-                o0[i] = fma(c3, prodn, pnew);
-            } else {
-                o0[i] = pnew;
-                o1[i] = prodn;
-            }
-        } else if (st.op == OP_P_PAIR1) {
-            const T tmp = fma(c1, e0[i], -s_);
-            o0[i] = (st.flags & F_PZERO) ? c2 * tmp : fma(c2, tmp, e1[i]);
-            if (!(st.flags & F_NO_O1)) o1[i] = tmp;
-        } else if (st.op == OP_P_PAIR2) {
-            const T prodn = fma(-c2, s_, e0[i]);
-            o0[i] = (st.flags & F_FINAL) ? fma(c3, prodn, e1[i]) : prodn;
-        }
-    }
-}
-
 // Synchronise the `rows` threads of one row group: the whole CTA when the
 // group is the CTA, else a named barrier of the group (ids 1..4; barrier 0
 // is __syncthreads).
@@ -274,103 +224,6 @@ __device__ __forceinline__ void bstep_tile(
             part[(size_t)vt * NR + tid] = t;
         }
     }
-}
-
-// Two tiles of one pass at once for the persistent kernel: the group's
-// thread gt owns row gt of tile vt (rows row0 .. row0 + rows) and row gt of
-// tile vt + 1, so that the gathers of both rows are in flight together
-// (the persistent kernel runs fewer threads per SM than the per-tile
-// kernel).  Each tile is uniform in its own system's step; a tile whose
-// step is a no-op or whose system has stopped is skipped.  The FP32 steps
-// of Algorithm 3 only (no OP_RESID).  srp holds 2 rows + 1 row pointers;
-// nvt = tiles of `rows` rows in the batch (tile vt + 1 may not exist).
-template <int NR>
-__device__ __forceinline__ void bstep_tile2(
-    int64_t vt, int64_t nvt, int rows, int gt, int group, float* sval, int32_t* scol, int32_t* srp,
-    int chunk,
-    const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-    const float* __restrict__ vals, const BStep* __restrict__ steps,
-    const int32_t* __restrict__ sys_of_tile, const BufSet<float>& b,
-    const int32_t* __restrict__ active) {
-    if (vt >= nvt) return;   // uniform over the group
-    const bool has_b = vt + 1 < nvt;
-    const int64_t row0 = vt * rows;
-    const int sa = sys_of_tile[row0 / BT];
-    const int sb = has_b ? sys_of_tile[(row0 + rows) / BT] : sa;
-    const BStep sta = steps[sa], stb = steps[sb];
-    const bool la = sta.op != OP_NOP && (!active || sys_live<NR>(active, sa));
-    const bool lb = has_b && stb.op != OP_NOP && (!active || sys_live<NR>(active, sb));
-    if (!la && !lb) return;   // uniform over the group
-    const int span = has_b ? 2 * rows : rows;
-    for (int i = gt; i <= span; i += rows) srp[i] = __ldg(rowptr + row0 + i);
-    group_sync(group, rows);
-    // stage only the live tiles' nonzeros
-    const int32_t k0 = la ? srp[0] : srp[rows];
-    const int32_t k1 = lb ? srp[2 * rows] : srp[rows];
-    const int32_t alo = la ? srp[gt] : k1, ahi = la ? srp[gt + 1] : k1;
-    const int32_t blo = lb ? srp[rows + gt] : k1, bhi = lb ? srp[rows + gt + 1] : k1;
-    const int64_t ra = row0 + gt, rb = row0 + rows + gt;
-    float ea0[NR], ea1[NR], eb0[NR], eb1[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) ea0[i] = ea1[i] = eb0[i] = eb1[i] = 0.f;
-    if (la && sta.a0 >= 0) ld_rhs<float, NR>(b.p[sta.a0] + ra * NR, ea0);
-    if (la && sta.a1 >= 0 && !(sta.flags & F_PZERO))
-#pragma unroll
-        for (int i = 0; i < NR; ++i) ea1[i] = b.p[sta.a1][ra * NR + i];
-    if (lb && stb.a0 >= 0) ld_rhs<float, NR>(b.p[stb.a0] + rb * NR, eb0);
-    if (lb && stb.a1 >= 0 && !(stb.flags & F_PZERO))
-#pragma unroll
-        for (int i = 0; i < NR; ++i) eb1[i] = b.p[stb.a1][rb * NR + i];
-    const float* xa = b.p[la ? sta.x : stb.x];
-    const float* xb = b.p[lb ? stb.x : sta.x];
-    float acca[NR], accb[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) acca[i] = accb[i] = 0.f;
-    for (int32_t c0 = k0; c0 < k1; c0 += chunk) {
-        const int32_t c1 = min(k1, c0 + chunk);
-        for (int32_t k = c0 + gt; k < c1; k += rows) {
-            const unsigned sv_ = (unsigned)__cvta_generic_to_shared(sval + (k - c0));
-            const unsigned sc_ = (unsigned)__cvta_generic_to_shared(scol + (k - c0));
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sv_), "l"(vals + k)
-                         : "memory");
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sc_), "l"(colind + k)
-                         : "memory");
-        }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        group_sync(group, rows);
-        int32_t ka = max(alo, c0) - c0, kb = max(blo, c0) - c0;
-        const int32_t ha = min(ahi, c1) - c0, hb = min(bhi, c1) - c0;
-        // both rows' nonzeros in lockstep (each row's sums in stored order)
-        for (; ka < ha && kb < hb; ++ka, ++kb) {
-            float x0[NR], x1[NR];
-            ld_rhs<float, NR>(xa + (int64_t)scol[ka] * NR, x0);
-            ld_rhs<float, NR>(xb + (int64_t)scol[kb] * NR, x1);
-            const float v0 = sval[ka], v1 = sval[kb];
-#pragma unroll
-            for (int i = 0; i < NR; ++i) {
-                acca[i] = fmaf(v0, x0[i], acca[i]);
-                accb[i] = fmaf(v1, x1[i], accb[i]);
-            }
-        }
-        for (; ka < ha; ++ka) {
-            float x0[NR];
-            ld_rhs<float, NR>(xa + (int64_t)scol[ka] * NR, x0);
-            const float v0 = sval[ka];
-#pragma unroll
-            for (int i = 0; i < NR; ++i) acca[i] = fmaf(v0, x0[i], acca[i]);
-        }
-        for (; kb < hb; ++kb) {
-            float x1[NR];
-            ld_rhs<float, NR>(xb + (int64_t)scol[kb] * NR, x1);
-            const float v1 = sval[kb];
-#pragma unroll
-            for (int i = 0; i < NR; ++i) accb[i] = fmaf(v1, x1[i], accb[i]);
-        }
-        group_sync(group, rows);
-    }
-    double sq[NR];
-    if (la) bstep_row_epilogue<float, NR>(sta, ra, acca, ea0, ea1, b, xa, sq);
-    if (lb) bstep_row_epilogue<float, NR>(stb, rb, accb, eb0, eb1, b, xb, sq);
 }
 
 // One pass of the batch over all tiles: one CTA per tile of blockDim.x rows.
@@ -918,7 +771,7 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
     // staging shared by the root-step phases (FP32: values then columns,
     // sliced per row group; FP64: the whole CTA)
     __shared__ __align__(16) unsigned char sraw[BCHUNK * (8 + 4)];
-    __shared__ int32_t srp[2 * BT + 8];
+    __shared__ int32_t srp[BT + 8];
     __shared__ double sred[8][NR];
     __shared__ double bd_sred[8][BCH][NR];
     __shared__ double bs_sh[ORTHO_MAXC][NR];
@@ -934,12 +787,10 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
     const int fchunk = BCHUNK * rows / 256;
     float* fsval = reinterpret_cast<float*>(sraw) + group * fchunk;
     int32_t* fscol = reinterpret_cast<int32_t*>(sraw + BCHUNK * 4) + group * fchunk;
-    int32_t* fsrp = srp + group * (2 * rows + 1);
+    int32_t* fsrp = srp + group * (rows + 1);
     double* dsval = reinterpret_cast<double*>(sraw);
     int32_t* dscol = reinterpret_cast<int32_t*>(sraw + BCHUNK * 8);
-    // CTA iterations of a root step: `groups` pairs of consecutive tiles each
-    const int64_t nvt_f = a.N / rows;   // tiles of `rows` rows
-    const int64_t nvb_f2 = (a.N / 256 + 1) / 2;
+    const int64_t nvb_f = a.N / 256;   // CTA iterations of a root step: `groups` tiles each
     int cycles = 0;
     for (int cyc = 0; cyc < a.max_cycles; ++cyc) {
         if (!any_active(a.st.active, nsolve)) break;
@@ -959,11 +810,10 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
             fs.p[B_C] = a.fc;
             for (int k = 0; k < a.K; ++k) {
                 const BStep* steps = a.steps_p + (size_t)k * a.nsys;
-                // each group takes two consecutive tiles (two rows per thread)
-                for (int64_t vb = blockIdx.x; vb < nvb_f2; vb += gridDim.x) {
-                    bstep_tile2<NR>(2 * (vb * groups + group), nvt_f, rows, gt, group, fsval,
-                                    fscol, fsrp, fchunk, a.rowptr, a.colind, a.v32, steps,
-                                    a.sys_of_tile, fs, a.st.active);
+                for (int64_t vb = blockIdx.x; vb < nvb_f; vb += gridDim.x) {
+                    bstep_tile<float, NR>(vb * groups + group, rows, gt, group, fsval, fscol, fsrp,
+                                          fchunk, sred, a.rowptr, a.colind, a.v32, steps,
+                                          a.sys_of_tile, fs, nullptr, a.st.active);
                     __syncthreads();
                 }
                 PSYNC();
