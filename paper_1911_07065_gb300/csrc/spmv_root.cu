@@ -526,6 +526,72 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
 template int32_t launch_step<double>(int, const StepArgs<double>&, cudaStream_t);
 template int32_t launch_step<float>(int, const StepArgs<float>&, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Small systems: a whole chain in one CTA
+// ---------------------------------------------------------------------------
+//
+// Below a few thousand rows a root step is a handful of CTAs and its cost is
+// the launch, not the bytes.  One CTA then runs all steps of the chain, a
+// barrier between consecutive steps, each row summed and updated exactly as
+// the per-step kernel does (one FMA per nonzero in stored order, the same
+// epilogue), so the results are bit-identical.  The vectors are written and
+// re-read inside the kernel, so they are read with plain loads (not the
+// read-only path); the matrix, which no step writes, through the read-only
+// path.
+
+template <typename T>
+struct SmallChain {
+    int32_t nsteps;
+    int32_t op[SMALL_MAX_STEPS];
+    StepArgs<T> st[SMALL_MAX_STEPS];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_chain(const SmallChain<T> c) {
+    for (int i = 0; i < c.nsteps; ++i) {
+        const StepArgs<T>& a = c.st[i];
+        const int op = c.op[i];
+        for (int32_t r = threadIdx.x; r < a.n; r += SMALL_THREADS) {
+            T acc = T(0);
+            for (int32_t k = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1); k < e; ++k)
+                acc = fma(__ldg(a.vals + k), a.x[__ldg(a.colind + k)], acc);
+            const T e0 = a.a0 ? a.a0[r] : T(0);
+            const T e1 = (a.a1 && !(a.flags & F_PZERO)) ? a.a1[r] : T(0);
+            const T e2 = (a.a2 && (a.flags & F_FINAL)) ? a.a2[r] : T(0);
+            double sq = 0.0;
+            switch (op) {
+                case OP_SPMV: step_epilogue<T, OP_SPMV>(a, r, acc, e0, e1, e2, sq); break;
+                case OP_PHI_REAL: step_epilogue<T, OP_PHI_REAL>(a, r, acc, e0, e1, e2, sq); break;
+                case OP_PHI_PAIR2: step_epilogue<T, OP_PHI_PAIR2>(a, r, acc, e0, e1, e2, sq); break;
+                case OP_P_REAL: step_epilogue<T, OP_P_REAL>(a, r, acc, e0, e1, e2, sq); break;
+                case OP_P_PAIR1: step_epilogue<T, OP_P_PAIR1>(a, r, acc, e0, e1, e2, sq); break;
+                default: step_epilogue<T, OP_P_PAIR2>(a, r, acc, e0, e1, e2, sq); break;
+            }
+        }
+        __syncthreads();   // this step's outputs are the next step's inputs
+    }
+}
+
+template <typename T>
+int32_t launch_small_chain(const StepArgs<T>* steps, const int* ops, int nsteps, cudaStream_t s) {
+    if (nsteps < 1 || nsteps > SMALL_MAX_STEPS) return PPG_ERR_ARG;
+    SmallChain<T> c;
+    c.nsteps = nsteps;
+    for (int i = 0; i < nsteps; ++i) {
+        if (ops[i] < OP_SPMV || ops[i] > OP_P_PAIR2 || ops[i] == OP_RESID ||
+            steps[i].n > SMALL_MAX_N)
+            return PPG_ERR_ARG;
+        c.op[i] = ops[i];
+        c.st[i] = steps[i];
+    }
+    k_small_chain<T><<<1, SMALL_THREADS, 0, s>>>(c);
+    ++g_launches;
+    return check_launch("k_small_chain");
+}
+
+template int32_t launch_small_chain<double>(const StepArgs<double>*, const int*, int, cudaStream_t);
+template int32_t launch_small_chain<float>(const StepArgs<float>*, const int*, int, cudaStream_t);
+
 // Unique bytes a step must move: the CSR (values, column indices, row
 // pointers) once, and each distinct length-n vector it reads or writes once.
 double step_bytes(int op, int flags, int64_t n, int64_t nnz, int elem) {
