@@ -42,7 +42,7 @@ namespace {
 
 constexpr int SW_THREADS = 256;    // threads per CTA; a thread owns two rows of a sub-tile
 constexpr int SW_SUB = 2 * SW_THREADS;   // rows per sub-tile
-constexpr int SW_CHUNK = 2048;     // nonzeros staged per chunk (16 KB)
+constexpr int SW_CHUNK = 4096;     // nonzeros staged per chunk (32 KB)
 
 // Shared memory of one tile: the staging chunk, tmp over the tile and its
 // halo, the halo list.
