@@ -774,6 +774,7 @@ def run_profile_case(name):
     ``batched_64x4``: one call of the batching form on its full workload;
     ``batched_16x4``: the same with its first 16 systems;
     ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix;
+    ``sweep_p_cd3d_160_f32``: the same through a fused-sweep plan;
     ``chain_phi_cd3d_160_f64`` / ``chain_p_cd3d_160_f32``: the 160^3 workload's
     degree-60 polynomial applied once (Algorithm 1 in FP64 / Algorithm 3 in
     FP32) after its construction, for in-chain captures."""
@@ -826,6 +827,18 @@ def run_profile_case(name):
         Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals, dtype=torch.float32)
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda().float()
         y = ppg.apply_poly(Ad, roots, v)
+    elif name == "sweep_p_cd3d_160_f32":
+        # Algorithm 3 in FP32 through a fused-sweep plan (tiles of 2048 rows,
+        # 16 x 16 x 8 blocks) with the precision workload's degree-60 polynomial
+        P = synth.problem("cd3d_160")
+        A = P.A
+        Ad = ppg.CSR.from_host(A.rowptr, A.colind, A.vals)
+        R = ppg.build_poly(Ad, P.d, torch.from_numpy(P.v0).cuda())
+        A32 = Ad.astype(torch.float32)
+        del Ad
+        plan = ppg.SweepPlan(A32, 2048, perm=synth.block_order((160, 160, 160), (16, 16, 8)))
+        v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda().float()
+        y = plan.apply_poly(R, v)
     elif name in ("chain_phi_cd3d_160_f64", "chain_p_cd3d_160_f32"):
         # the precision workload's own degree-60 polynomial (60 SpMV launches
         # of the construction), then one whole chain: Algorithm 1 in FP64 or
