@@ -140,38 +140,6 @@ static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const in
                          bool reserve_l2) {
     double bytes = 0.0;
     const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3, reserve_l2);
-    // a small system: the whole range of steps in one CTA (no degree-one
-    // update among them)
-    bool small = n <= SMALL_MAX_N && i1 - i0 >= 2 && i1 - i0 <= SMALL_MAX_STEPS;
-    for (int i = i0; small && i < i1; ++i) small = plan[(size_t)i].op != OP_AXPY;
-    if (small) {
-        StepArgs<T> sa[SMALL_MAX_STEPS];
-        int ops[SMALL_MAX_STEPS];
-        for (int i = i0; i < i1; ++i) {
-            const Step& st = plan[(size_t)i];
-            StepArgs<T>& a = sa[i - i0];
-            a = StepArgs<T>{};
-            a.rowptr = rowptr;
-            a.colind = colind;
-            a.vals = vals;
-            a.n = n;
-            a.x = cbuf<T>(bufs, st.x);
-            a.a0 = cbuf<T>(bufs, st.a0);
-            a.a1 = cbuf<T>(bufs, st.a1);
-            a.a2 = cbuf<T>(bufs, st.a2);
-            a.o0 = mbuf<T>(bufs, st.o0);
-            a.o1 = mbuf<T>(bufs, st.o1);
-            a.c1 = (T)st.c1;
-            a.c2 = (T)st.c2;
-            a.c3 = (T)st.c3;
-            a.flags = st.flags;
-            ops[i - i0] = st.op;
-            bytes += step_bytes(st.op, st.flags, n, nnz, (int)sizeof(T));
-        }
-        PPG_TRY(launch_small_chain<T>(sa, ops, i1 - i0, s));
-        if (bytes_out) *bytes_out = bytes;
-        return PPG_OK;
-    }
     for (int i = i0; i < i1; ++i) {
         const Step& st = plan[(size_t)i];
         if (st.op == OP_AXPY) {

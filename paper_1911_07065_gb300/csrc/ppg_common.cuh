@@ -152,17 +152,6 @@ struct StepArgs {
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a, cudaStream_t s);
 
-// Small systems: every step of a chain in one CTA of SMALL_THREADS threads
-// with the chain's vectors (at most SMALL_MAX_SLOTS distinct) in shared
-// memory (n <= SMALL_MAX_N, at most SMALL_MAX_STEPS steps, no OP_RESID, one
-// matrix), results bit-identical to launching the steps one by one.
-constexpr int SMALL_THREADS = 1024;
-constexpr int SMALL_MAX_STEPS = 64;
-constexpr int SMALL_MAX_SLOTS = 6;
-constexpr int32_t SMALL_MAX_N = 4096;
-template <typename T>
-int32_t launch_small_chain(const StepArgs<T>* steps, const int* ops, int nsteps, cudaStream_t s);
-
 // a root step with the operator product precomputed in prodv (composite
 // operators); returns the grid (= partial sums for OP_RESID) or a status
 template <typename T>

@@ -25,7 +25,6 @@
 // chain (every root reads the same A); otherwise with evict-first, so that
 // streaming A does not push the vectors out.
 #include <atomic>
-#include <cstring>
 
 #include "ppg_common.cuh"
 
@@ -526,148 +525,6 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
 
 template int32_t launch_step<double>(int, const StepArgs<double>&, cudaStream_t);
 template int32_t launch_step<float>(int, const StepArgs<float>&, cudaStream_t);
-
-// ---------------------------------------------------------------------------
-// Small systems: a whole chain in one CTA
-// ---------------------------------------------------------------------------
-//
-// Below a few thousand rows a root step is a handful of CTAs and its cost is
-// the launch, not the bytes.  One CTA then runs all steps of the chain with
-// the chain's vectors in shared memory (each distinct vector of the steps is
-// a slot: loaded once at the start, written back at the end if a step wrote
-// it), a barrier between consecutive steps, and each row summed and updated
-// exactly as the per-step kernel does (one FMA per nonzero in stored order,
-// the same epilogue), so the results are bit-identical.
-
-template <typename T>
-struct SmallChain {
-    int32_t n, nsteps, nslots;
-    const int32_t* rowptr;
-    const int32_t* colind;
-    const T* vals;
-    T* gvec[SMALL_MAX_SLOTS];        // the slots' vectors in global memory
-    int32_t load[SMALL_MAX_SLOTS];   // read by some step: loaded at the start
-    int32_t store[SMALL_MAX_SLOTS];  // written by some step: stored at the end
-    int32_t op[SMALL_MAX_STEPS];
-    int8_t slot[SMALL_MAX_STEPS][6]; // x, a0, a1, a2, o0, o1 (-1: none)
-    T c1[SMALL_MAX_STEPS], c2[SMALL_MAX_STEPS], c3[SMALL_MAX_STEPS];
-    int32_t flags[SMALL_MAX_STEPS];
-};
-
-template <typename T>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_chain(const SmallChain<T> c) {
-    extern __shared__ __align__(16) unsigned char small_raw[];
-    T* vec = reinterpret_cast<T*>(small_raw);
-    const int32_t n = c.n;
-    for (int j = 0; j < c.nslots; ++j)
-        if (c.load[j])
-            for (int32_t r = threadIdx.x; r < n; r += SMALL_THREADS) vec[(size_t)j * n + r] = c.gvec[j][r];
-    __syncthreads();
-    for (int i = 0; i < c.nsteps; ++i) {
-        StepArgs<T> a{};
-        a.n = n;
-        T* sp[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sp[q] = c.slot[i][q] >= 0 ? vec + (size_t)c.slot[i][q] * n : nullptr;
-        a.x = sp[0];
-        a.a0 = sp[1];
-        a.a1 = sp[2];
-        a.a2 = sp[3];
-        a.o0 = sp[4];
-        a.o1 = sp[5];
-        a.c1 = c.c1[i];
-        a.c2 = c.c2[i];
-        a.c3 = c.c3[i];
-        a.flags = c.flags[i];
-        const int op = c.op[i];
-        for (int32_t r = threadIdx.x; r < n; r += SMALL_THREADS) {
-            T acc = T(0);
-            for (int32_t k = __ldg(c.rowptr + r), e = __ldg(c.rowptr + r + 1); k < e; ++k)
-                acc = fma(__ldg(c.vals + k), a.x[__ldg(c.colind + k)], acc);
-            const T e0 = a.a0 ? a.a0[r] : T(0);
-            const T e1 = (a.a1 && !(a.flags & F_PZERO)) ? a.a1[r] : T(0);
-            const T e2 = (a.a2 && (a.flags & F_FINAL)) ? a.a2[r] : T(0);
-            double sq = 0.0;
-            switch (op) {
-                case OP_SPMV: step_epilogue<T, OP_SPMV>(a, r, acc, e0, e1, e2, sq); break;
-                case OP_PHI_REAL: step_epilogue<T, OP_PHI_REAL>(a, r, acc, e0, e1, e2, sq); break;
-                case OP_PHI_PAIR2: step_epilogue<T, OP_PHI_PAIR2>(a, r, acc, e0, e1, e2, sq); break;
-                case OP_P_REAL: step_epilogue<T, OP_P_REAL>(a, r, acc, e0, e1, e2, sq); break;
-                case OP_P_PAIR1: step_epilogue<T, OP_P_PAIR1>(a, r, acc, e0, e1, e2, sq); break;
-                default: step_epilogue<T, OP_P_PAIR2>(a, r, acc, e0, e1, e2, sq); break;
-            }
-        }
-        __syncthreads();   // this step's outputs are the next step's inputs
-    }
-    for (int j = 0; j < c.nslots; ++j)
-        if (c.store[j])
-            for (int32_t r = threadIdx.x; r < n; r += SMALL_THREADS) c.gvec[j][r] = vec[(size_t)j * n + r];
-}
-
-template <typename T>
-int32_t launch_small_chain(const StepArgs<T>* steps, const int* ops, int nsteps, cudaStream_t s) {
-    if (nsteps < 1 || nsteps > SMALL_MAX_STEPS) return PPG_ERR_ARG;
-    SmallChain<T> c;
-    std::memset(&c, 0, sizeof(c));
-    c.n = steps[0].n;
-    c.nsteps = nsteps;
-    c.rowptr = steps[0].rowptr;
-    c.colind = steps[0].colind;
-    c.vals = steps[0].vals;
-    if (c.n < 1 || c.n > SMALL_MAX_N) return PPG_ERR_ARG;
-    auto slot_of = [&](const T* p, bool write) -> int {
-        if (!p) return -1;
-        for (int j = 0; j < c.nslots; ++j)
-            if (c.gvec[j] == p) {
-                if (write) c.store[j] = 1;
-                return j;
-            }
-        if (c.nslots == SMALL_MAX_SLOTS) return -2;
-        c.gvec[c.nslots] = const_cast<T*>(p);
-        c.load[c.nslots] = write ? 0 : 1;
-        c.store[c.nslots] = write ? 1 : 0;
-        return c.nslots++;
-    };
-    for (int i = 0; i < nsteps; ++i) {
-        const StepArgs<T>& a = steps[i];
-        if (ops[i] < OP_SPMV || ops[i] > OP_P_PAIR2 || ops[i] == OP_RESID || a.n != c.n ||
-            a.rowptr != c.rowptr)
-            return PPG_ERR_ARG;
-        c.op[i] = ops[i];
-        // inputs first: a vector read by a step before any step writes it is loaded
-        const bool rd_a1 = !(a.flags & F_PZERO), rd_a2 = (a.flags & F_FINAL) != 0;
-        const int sx = slot_of(a.x, false);
-        const int s0 = slot_of(a.a0, false);
-        const int s1 = rd_a1 ? slot_of(a.a1, false) : -1;
-        const int s2 = rd_a2 ? slot_of(a.a2, false) : -1;
-        const int so0 = slot_of(a.o0, true);
-        const bool w1 = !(ops[i] == OP_P_PAIR1 && (a.flags & F_NO_O1)) &&
-                        !(ops[i] == OP_P_REAL && (a.flags & F_FINAL));
-        const int so1 = w1 ? slot_of(a.o1, true) : -1;
-        const int sl[6] = {sx, s0, s1, s2, so0, so1};
-        for (int q = 0; q < 6; ++q) {
-            if (sl[q] == -2) return PPG_ERR_ARG;
-            c.slot[i][q] = (int8_t)sl[q];
-        }
-        c.c1[i] = a.c1;
-        c.c2[i] = a.c2;
-        c.c3[i] = a.c3;
-        c.flags[i] = a.flags;
-    }
-    const size_t smem = (size_t)c.nslots * c.n * sizeof(T);
-    static bool attr_done[2] = {false, false};
-    if (!attr_done[sizeof(T) == 8]) {
-        cudaFuncSetAttribute(k_small_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)SMALL_MAX_SLOTS * SMALL_MAX_N * sizeof(T)));
-        attr_done[sizeof(T) == 8] = true;
-    }
-    k_small_chain<T><<<1, SMALL_THREADS, smem, s>>>(c);
-    ++g_launches;
-    return check_launch("k_small_chain");
-}
-
-template int32_t launch_small_chain<double>(const StepArgs<double>*, const int*, int, cudaStream_t);
-template int32_t launch_small_chain<float>(const StepArgs<float>*, const int*, int, cudaStream_t);
 
 // Unique bytes a step must move: the CSR (values, column indices, row
 // pointers) once, and each distinct length-n vector it reads or writes once.
