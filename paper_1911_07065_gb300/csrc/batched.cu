@@ -735,7 +735,7 @@ __device__ bool grid_sync(GridBar* gb, unsigned long long timeout_ns) {
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                if (it > 64) __nanosleep(32);   // spin briefly before backing off
             }
         }
         if (*verr != 0u) ok = 0;
