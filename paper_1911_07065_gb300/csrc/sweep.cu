@@ -18,6 +18,12 @@
 // nonzero in the row's stored order, the same epilogue forms.  A symmetric
 // permutation keeps each row's entries in their order, so the result is
 // bit-identical to ppg_apply_poly on the original matrix.
+//
+// Measured on GB300 (160^3, 16 x 16 x 8 blocks): a pair moves 39 % fewer DRAM
+// bytes than the two unfused passes but takes about twice as long -- each
+// CTA runs its two phases over a whole tile back to back and the kernel is
+// bound by the latency of its gathers -- so the solver's default remains the
+// one-pass-per-root chain, and plans are an explicit choice of the caller.
 #include <algorithm>
 #include <cstring>
 #include <vector>
