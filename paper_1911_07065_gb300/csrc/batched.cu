@@ -150,19 +150,8 @@ __device__ __forceinline__ void bstep_tile(
         group_sync(group, rows);
         const int32_t lo = max(lo_r, c0) - c0, hi = min(hi_r, c1) - c0;
         int32_t k = lo;
-        // one FMA per nonzero and right-hand side, the gathers of four (then
-        // two) nonzeros in flight before their multiply-adds
-        for (; k + 4 <= hi; k += 4) {
-            T x0[NR], x1[NR], x2[NR], x3[NR];
-            ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
-            ld_rhs<T, NR>(x + (int64_t)scol[k + 1] * NR, x1);
-            ld_rhs<T, NR>(x + (int64_t)scol[k + 2] * NR, x2);
-            ld_rhs<T, NR>(x + (int64_t)scol[k + 3] * NR, x3);
-            const T v0 = sval[k], v1 = sval[k + 1], v2 = sval[k + 2], v3 = sval[k + 3];
-#pragma unroll
-            for (int i = 0; i < NR; ++i)
-                acc[i] = fma(v3, x3[i], fma(v2, x2[i], fma(v1, x1[i], fma(v0, x0[i], acc[i]))));
-        }
+        // one FMA per nonzero and right-hand side, the gathers of two
+        // nonzeros (2 NR values) in flight before their multiply-adds
         for (; k + 2 <= hi; k += 2) {
             T x0[NR], x1[NR];
             ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
