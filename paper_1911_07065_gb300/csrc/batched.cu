@@ -767,7 +767,7 @@ __device__ __forceinline__ bool any_active(const int32_t* active, int nsolve) {
     } while (0)
 
 template <int NR>
-__global__ void __launch_bounds__(256, 5) k_bpersist(const PArgs a) {
+__global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
     // staging shared by the root-step phases (FP32: values then columns,
     // sliced per row group; FP64: the whole CTA)
     __shared__ __align__(16) unsigned char sraw[BCHUNK * (8 + 4)];
