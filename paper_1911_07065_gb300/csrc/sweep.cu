@@ -167,6 +167,7 @@ k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col
     int32_t* halo_s = reinterpret_cast<int32_t*>(tmp_own + SW_SUB + hq_alloc);
     const int tid = threadIdx.x;
     for (int i = tid; i < nh; i += SW_THREADS) halo_s[i] = halo_idx[h0 + i];
+    __syncthreads();   // the halo list is read below by other threads (a CTA may own no rows)
 
     // phase A, own rows
     {
