@@ -24,8 +24,6 @@
 // CTA runs its two phases over a whole tile back to back and the kernel is
 // bound by the latency of its gathers -- so the solver's default remains the
 // one-pass-per-root chain, and plans are an explicit choice of the caller.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -48,20 +46,15 @@ struct ppg_sweep_plan {
 namespace ppg {
 namespace {
 
-constexpr int SW_THREADS = 256;    // threads per CTA; a thread owns two rows
-constexpr int SW_SUB = 2 * SW_THREADS;   // rows per CTA of a tile
-constexpr int SW_MAX_CL = 8;       // CTAs per tile (a thread-block cluster), portable maximum
+constexpr int SW_THREADS = 256;    // threads per CTA; a thread owns two rows of a sub-tile
+constexpr int SW_SUB = 2 * SW_THREADS;   // rows per sub-tile
 constexpr int SW_CHUNK = 4096;     // nonzeros staged per chunk (32 KB)
 
-int sweep_cluster(int T) { return (T + SW_SUB - 1) / SW_SUB; }
-
-// Shared memory of one CTA: the staging chunk, the tmp values this CTA owns
-// (its rows and its share of the halo), the tile's halo list.
+// Shared memory of one tile: the staging chunk, tmp over the tile and its
+// halo, the halo list.
 size_t sweep_smem(int T, int halo) {
-    const int cl = sweep_cluster(T);
-    const int hq = (halo + cl - 1) / cl;
     return (size_t)SW_CHUNK * (sizeof(float) + sizeof(int32_t)) +
-           (size_t)(SW_SUB + hq) * sizeof(float) + (size_t)halo * sizeof(int32_t);
+           (size_t)(T + halo) * sizeof(float) + (size_t)halo * sizeof(int32_t);
 }
 
 __device__ __forceinline__ int halo_slot(const int32_t* h, int nh, int32_t c) {
@@ -104,131 +97,120 @@ __device__ __forceinline__ void sw_two_rows(const float* sval, const int32_t* sc
     for (; kb < hb; ++kb) acc_b = fmaf(sval[kb], X(scol[kb]), acc_b);
 }
 
-// A * vector over rows [r0, r0 + nr) (nr <= SW_SUB), two rows per thread,
-// the rows' nonzeros staged in shared memory in chunks (any row length);
-// row r0 + tid goes to acc_a, row r0 + tid + SW_THREADS to acc_b.
-template <typename XF>
-__device__ __forceinline__ void sw_rows_product(const int32_t* __restrict__ rowptr,
-                                                const int32_t* __restrict__ colind,
-                                                const float* __restrict__ vals, int32_t r0,
-                                                int nr, float* sval, int32_t* scol,
-                                                float& acc_a, float& acc_b, XF X) {
-    const int tid = threadIdx.x;
-    acc_a = acc_b = 0.f;
-    if (nr <= 0) return;   // uniform over the CTA
-    const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
-    const int ia = tid, ib = tid + SW_THREADS;
-    const int32_t alo = ia < nr ? __ldg(rowptr + r0 + ia) : k1;
-    const int32_t ahi = ia < nr ? __ldg(rowptr + r0 + ia + 1) : k1;
-    const int32_t blo = ib < nr ? __ldg(rowptr + r0 + ib) : k1;
-    const int32_t bhi = ib < nr ? __ldg(rowptr + r0 + ib + 1) : k1;
-    for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
-        const int32_t ce = min(k1, c0 + SW_CHUNK);
-        sw_stage(sval, scol, vals, colind, c0, ce);
-        __syncthreads();
-        sw_two_rows(sval, scol, max(alo, c0) - c0, min(ahi, ce) - c0, max(blo, c0) - c0,
-                    min(bhi, ce) - c0, acc_a, acc_b, X);
-        __syncthreads();
-    }
-}
-
-// One conjugate pair over one tile, on a cluster of CL CTAs (CL = tile rows
-// / 512, rounded up): CTA q owns rows q*512 .. of the tile and a CL-th of
-// the tile's halo.  Phase A: each CTA computes tmp = c1 prod - A prod for
-// its rows and its halo share into its own shared memory, and p' for its
-// rows.  A cluster barrier.  Phase B: each CTA computes prod' = prod - c2 A
-// tmp for its rows, reading tmp from the shared memory of whichever CTA of
-// the cluster owns the column (distributed shared memory).  A second
-// barrier keeps every CTA's shared memory alive until the others are done.
-// prod = a0 of both steps, p = the accumulator (a1 of P_PAIR1, read unless
-// PZERO), pout = o0 of P_PAIR1 (p'), qout = o0 of P_PAIR2 (prod', or p''
-// when FINAL: qout = pout then).
+// One conjugate pair over one tile (see the file comment).  prod = a0 of
+// both steps, p = the accumulator (a1 of P_PAIR1, read unless PZERO),
+// pout = o0 of P_PAIR1 (p'), qout = o0 of P_PAIR2 (prod', or p'' when
+// FINAL: qout = pout then, and p' goes through pout between the phases).
+// The tile's rows go in sub-tiles of SW_SUB rows, two per thread, whose
+// nonzeros are staged in shared memory by coalesced copies (in chunks, so
+// any row length works); each row sums its products in stored order, as
+// the unfused kernel does.
 __global__ void __launch_bounds__(SW_THREADS)
 k_sweep_pair(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-             const float* __restrict__ vals, int32_t n, int T, int CL, int hq_alloc,
+             const float* __restrict__ vals, int32_t n, int T,
              const int32_t* __restrict__ halo_off, const int32_t* __restrict__ halo_idx,
              const float* __restrict__ prod, const float* p, float* pout, float* qout,
              float c1, float c2, float c3, int pzero, int final_) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char sw_raw[];
-    const int q = (int)cluster.block_rank();
-    const int tile = blockIdx.x / CL;
+    const int tile = blockIdx.x;
     const int32_t lo = tile * T;
     const int rows = min(T, n - lo);
-    const int32_t my0 = lo + q * SW_SUB;
-    const int my_nr = max(0, min(SW_SUB, rows - q * SW_SUB));
     const int h0 = halo_off[tile], nh = halo_off[tile + 1] - h0;
-    const int hq = (nh + CL - 1) / CL;
-    const int my_h0 = q * hq, my_nh = max(0, min(hq, nh - my_h0));
     float* sval = reinterpret_cast<float*>(sw_raw);
     int32_t* scol = reinterpret_cast<int32_t*>(sval + SW_CHUNK);
-    float* tmp_own = reinterpret_cast<float*>(scol + SW_CHUNK);   // [SW_SUB + hq_alloc]
-    int32_t* halo_s = reinterpret_cast<int32_t*>(tmp_own + SW_SUB + hq_alloc);
+    float* tmp_s = reinterpret_cast<float*>(scol + SW_CHUNK);   // [T + nh]
+    int32_t* halo_s = reinterpret_cast<int32_t*>(tmp_s + T + nh);
     const int tid = threadIdx.x;
     for (int i = tid; i < nh; i += SW_THREADS) halo_s[i] = halo_idx[h0 + i];
-    __syncthreads();   // the halo list is read below by other threads (a CTA may own no rows)
+    __syncthreads();   // the halo list is read by other threads below
+    auto xprod = [&](int32_t c) { return __ldg(prod + c); };
 
-    // phase A, own rows
-    {
-        float acc_a, acc_b;
-        sw_rows_product(rowptr, colind, vals, my0, my_nr, sval, scol, acc_a, acc_b,
-                        [&](int32_t c) { return __ldg(prod + c); });
+    // phase A, tile rows: tmp = c1 prod - A prod; p'
+    for (int sub = 0; sub < rows; sub += SW_SUB) {
+        const int32_t r0 = lo + sub;
+        const int nr = min(SW_SUB, rows - sub);
+        const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
+        const int ia = tid, ib = tid + SW_THREADS;
+        const int32_t alo = ia < nr ? __ldg(rowptr + r0 + ia) : k1;
+        const int32_t ahi = ia < nr ? __ldg(rowptr + r0 + ia + 1) : k1;
+        const int32_t blo = ib < nr ? __ldg(rowptr + r0 + ib) : k1;
+        const int32_t bhi = ib < nr ? __ldg(rowptr + r0 + ib + 1) : k1;
+        float acc_a = 0.f, acc_b = 0.f;
+        for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
+            const int32_t ce = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, ce);
+            __syncthreads();
+            sw_two_rows(sval, scol, max(alo, c0) - c0, min(ahi, ce) - c0, max(blo, c0) - c0,
+                        min(bhi, ce) - c0, acc_a, acc_b, xprod);
+            __syncthreads();
+        }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = tid + k * SW_THREADS;
-            if (i < my_nr) {
-                const int32_t g = my0 + i;
-                const float tmp = fmaf(c1, __ldg(prod + g), -(k ? acc_b : acc_a));
-                tmp_own[i] = tmp;
+        for (int q = 0; q < 2; ++q) {
+            const int i = q ? ib : ia;
+            if (i < nr) {
+                const int32_t g = r0 + i;
+                const float tmp = fmaf(c1, __ldg(prod + g), -(q ? acc_b : acc_a));
+                tmp_s[sub + i] = tmp;
                 pout[g] = pzero ? c2 * tmp : fmaf(c2, tmp, p[g]);
             }
         }
     }
-    // phase A, own share of the halo rows (rows of other tiles), from global memory
-    for (int j = tid; j < my_nh; j += SW_THREADS) {
-        const int32_t g = halo_s[my_h0 + j];
-        float acc = 0.f;
-        int32_t k = __ldg(rowptr + g);
-        const int32_t e = __ldg(rowptr + g + 1);
-        for (; k + 2 <= e; k += 2) {
-            const float x0 = __ldg(prod + __ldg(colind + k)), x1 = __ldg(prod + __ldg(colind + k + 1));
-            acc = fmaf(__ldg(vals + k), x0, acc);
-            acc = fmaf(__ldg(vals + k + 1), x1, acc);
+    // phase A, halo rows: the same tmp, two rows per thread from global memory
+    for (int li = tid; li < nh; li += 2 * SW_THREADS) {
+        const int lj = li + SW_THREADS;
+        const int32_t ga = halo_s[li];
+        const int32_t gb = lj < nh ? halo_s[lj] : ga;
+        int32_t ka = __ldg(rowptr + ga), kb = __ldg(rowptr + gb);
+        const int32_t ea = __ldg(rowptr + ga + 1), eb = lj < nh ? __ldg(rowptr + gb + 1) : kb;
+        float acc_a = 0.f, acc_b = 0.f;
+        for (; ka + 2 <= ea && kb + 2 <= eb; ka += 2, kb += 2) {
+            const float xa0 = __ldg(prod + __ldg(colind + ka)), xa1 = __ldg(prod + __ldg(colind + ka + 1));
+            const float xb0 = __ldg(prod + __ldg(colind + kb)), xb1 = __ldg(prod + __ldg(colind + kb + 1));
+            acc_a = fmaf(__ldg(vals + ka), xa0, acc_a);
+            acc_a = fmaf(__ldg(vals + ka + 1), xa1, acc_a);
+            acc_b = fmaf(__ldg(vals + kb), xb0, acc_b);
+            acc_b = fmaf(__ldg(vals + kb + 1), xb1, acc_b);
         }
-        for (; k < e; ++k) acc = fmaf(__ldg(vals + k), __ldg(prod + __ldg(colind + k)), acc);
-        tmp_own[SW_SUB + j] = fmaf(c1, __ldg(prod + g), -acc);
+        for (; ka < ea; ++ka) acc_a = fmaf(__ldg(vals + ka), __ldg(prod + __ldg(colind + ka)), acc_a);
+        for (; kb < eb; ++kb) acc_b = fmaf(__ldg(vals + kb), __ldg(prod + __ldg(colind + kb)), acc_b);
+        tmp_s[T + li] = fmaf(c1, __ldg(prod + ga), -acc_a);
+        if (lj < nh) tmp_s[T + lj] = fmaf(c1, __ldg(prod + gb), -acc_b);
     }
-    cluster.sync();   // every CTA's tmp (and p') complete and visible to the cluster
-    // phase B, own rows: tmp of a tile column from its owner CTA, of a halo
-    // column from the CTA that computed it
-    {
-        auto xtmp = [&](int32_t c) {
-            int owner, idx;
-            if (c >= lo && c < lo + rows) {
-                owner = (c - lo) / SW_SUB;
-                idx = (c - lo) - owner * SW_SUB;
-            } else {
-                const int h = halo_slot(halo_s, nh, c);
-                owner = h / hq;
-                idx = SW_SUB + (h - owner * hq);
-            }
-            const float* src = owner == q ? tmp_own : cluster.map_shared_rank(tmp_own, owner);
-            return src[idx];
-        };
-        float acc_a, acc_b;
-        sw_rows_product(rowptr, colind, vals, my0, my_nr, sval, scol, acc_a, acc_b, xtmp);
+    __syncthreads();   // tmp complete; p' of the tile written (read back below when FINAL)
+    // phase B: prod' = prod - c2 A tmp for the tile's rows, tmp from shared
+    // memory (tile columns by offset, halo columns by binary search); the
+    // tile's nonzeros are staged again (from L2: this CTA read them just now)
+    auto xtmp = [&](int32_t c) {
+        return (c >= lo && c < lo + rows) ? tmp_s[c - lo] : tmp_s[T + halo_slot(halo_s, nh, c)];
+    };
+    for (int sub = 0; sub < rows; sub += SW_SUB) {
+        const int32_t r0 = lo + sub;
+        const int nr = min(SW_SUB, rows - sub);
+        const int32_t k0 = __ldg(rowptr + r0), k1 = __ldg(rowptr + r0 + nr);
+        const int ia = tid, ib = tid + SW_THREADS;
+        const int32_t alo = ia < nr ? __ldg(rowptr + r0 + ia) : k1;
+        const int32_t ahi = ia < nr ? __ldg(rowptr + r0 + ia + 1) : k1;
+        const int32_t blo = ib < nr ? __ldg(rowptr + r0 + ib) : k1;
+        const int32_t bhi = ib < nr ? __ldg(rowptr + r0 + ib + 1) : k1;
+        float acc_a = 0.f, acc_b = 0.f;
+        for (int32_t c0 = k0; c0 < k1; c0 += SW_CHUNK) {
+            const int32_t ce = min(k1, c0 + SW_CHUNK);
+            sw_stage(sval, scol, vals, colind, c0, ce);
+            __syncthreads();
+            sw_two_rows(sval, scol, max(alo, c0) - c0, min(ahi, ce) - c0, max(blo, c0) - c0,
+                        min(bhi, ce) - c0, acc_a, acc_b, xtmp);
+            __syncthreads();
+        }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int i = tid + k * SW_THREADS;
-            if (i < my_nr) {
-                const int32_t g = my0 + i;
-                const float prodn = fmaf(-c2, k ? acc_b : acc_a, __ldg(prod + g));
+        for (int q = 0; q < 2; ++q) {
+            const int i = q ? ib : ia;
+            if (i < nr) {
+                const int32_t g = r0 + i;
+                const float prodn = fmaf(-c2, q ? acc_b : acc_a, __ldg(prod + g));
                 qout[g] = final_ ? fmaf(c3, prodn, pout[g]) : prodn;
             }
         }
     }
-    cluster.sync();   // the others may still read this CTA's tmp
 }
 
 // y[i] = x[perm[i]] (cast: FP64 source into the FP32 permuted vector)
@@ -310,32 +292,13 @@ int32_t sweep_run_chain(const ppg_sweep_plan* P, const std::vector<Step>& plan,
             plan[i + 1].op == OP_P_PAIR2) {
             const Step& s2 = plan[i + 1];
             const bool fin = s2.flags & F_FINAL;
-            const int CL = sweep_cluster(P->T);
-            const int hq_alloc = (P->max_halo + CL - 1) / CL;
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)(P->ntiles * CL));
-            cfg.blockDim = dim3(SW_THREADS);
-            cfg.dynamicSmemBytes = smem;
-            cfg.stream = s;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)CL;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            const cudaError_t e = cudaLaunchKernelEx(
-                &cfg, k_sweep_pair, (const int32_t*)P->rowptr, (const int32_t*)P->colind,
-                (const float*)P->vals, n, P->T, CL, hq_alloc, (const int32_t*)P->halo_off,
-                (const int32_t*)P->halo_idx, (const float*)bufs.ptr[st.a0],
-                (st.flags & F_PZERO) ? (const float*)nullptr : (const float*)bufs.ptr[st.a1],
-                (float*)bufs.ptr[st.o0],
-                fin ? (float*)bufs.ptr[st.o0] : (float*)bufs.ptr[s2.o0], (float)st.c1,
-                (float)st.c2, (float)s2.c3, (st.flags & F_PZERO) ? 1 : 0, fin ? 1 : 0);
-            if (e != cudaSuccess) {
-                set_cuda_error(e, "cudaLaunchKernelEx(k_sweep_pair)");
-                return PPG_ERR_CUDA;
-            }
+            k_sweep_pair<<<P->ntiles, SW_THREADS, smem, s>>>(
+                P->rowptr, P->colind, P->vals, n, P->T, P->halo_off, P->halo_idx,
+                (const float*)bufs.ptr[st.a0],
+                (st.flags & F_PZERO) ? nullptr : (const float*)bufs.ptr[st.a1],
+                (float*)bufs.ptr[st.o0], fin ? (float*)bufs.ptr[st.o0] : (float*)bufs.ptr[s2.o0],
+                (float)st.c1, (float)st.c2, (float)s2.c3, (st.flags & F_PZERO) ? 1 : 0,
+                fin ? 1 : 0);
             ++g_launches;
             PPG_TRY(check_launch("k_sweep_pair"));
             ++i;
@@ -502,7 +465,7 @@ int32_t ppg_sweep_plan_create(const ppg_csr* A, const int32_t* perm_host, int32_
     PPG_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->dev));
     const size_t need = sweep_smem(T, max_halo);
     P->fused = (fuse != 0 && (double)P->halo_total <= 0.6 * (double)n &&
-                sweep_cluster(T) <= SW_MAX_CL && need <= (size_t)smem_max) ? 1 : 0;
+                need <= (size_t)smem_max) ? 1 : 0;
     // one device allocation, owned by the plan
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_rp = al(sizeof(int32_t) * (n + 1)), b_ci = al(sizeof(int32_t) * std::max(nnz, 1));
