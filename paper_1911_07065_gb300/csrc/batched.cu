@@ -104,7 +104,7 @@ __device__ __forceinline__ void group_sync(int group, int rows) {
 // leaves everything untouched.  OP_RESID writes the tile's partial sums of
 // squares, part[vt * NR + k] (only with rows == blockDim.x).  The staging
 // buffers sval / scol hold `chunk` nonzeros, srp rows + 1 row pointers.
-template <typename T, int NR, int DEPTH = 2>
+template <typename T, int NR>
 __device__ __forceinline__ void bstep_tile(
     int64_t vt, int rows, int gt, int group, T* sval, int32_t* scol, int32_t* srp, int chunk,
     double (*sred)[NR], const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
@@ -150,21 +150,8 @@ __device__ __forceinline__ void bstep_tile(
         group_sync(group, rows);
         const int32_t lo = max(lo_r, c0) - c0, hi = min(hi_r, c1) - c0;
         int32_t k = lo;
-        // one FMA per nonzero and right-hand side, the gathers of DEPTH (then
-        // two) nonzeros in flight before their multiply-adds; sums in order
-        if constexpr (DEPTH == 4) {
-            for (; k + 4 <= hi; k += 4) {
-                T x0[NR], x1[NR], x2[NR], x3[NR];
-                ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
-                ld_rhs<T, NR>(x + (int64_t)scol[k + 1] * NR, x1);
-                ld_rhs<T, NR>(x + (int64_t)scol[k + 2] * NR, x2);
-                ld_rhs<T, NR>(x + (int64_t)scol[k + 3] * NR, x3);
-                const T v0 = sval[k], v1 = sval[k + 1], v2 = sval[k + 2], v3 = sval[k + 3];
-#pragma unroll
-                for (int i = 0; i < NR; ++i)
-                    acc[i] = fma(v3, x3[i], fma(v2, x2[i], fma(v1, x1[i], fma(v0, x0[i], acc[i]))));
-            }
-        }
+        // one FMA per nonzero and right-hand side, the gathers of two
+        // nonzeros (2 NR values) in flight before their multiply-adds
         for (; k + 2 <= hi; k += 2) {
             T x0[NR], x1[NR];
             ld_rhs<T, NR>(x + (int64_t)scol[k] * NR, x0);
@@ -824,8 +811,7 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
             for (int k = 0; k < a.K; ++k) {
                 const BStep* steps = a.steps_p + (size_t)k * a.nsys;
                 for (int64_t vb = blockIdx.x; vb < nvb_f; vb += gridDim.x) {
-                    // four nonzeros' gathers in flight: this kernel's registers allow it
-                    bstep_tile<float, NR, 4>(vb * groups + group, rows, gt, group, fsval, fscol, fsrp,
+                    bstep_tile<float, NR>(vb * groups + group, rows, gt, group, fsval, fscol, fsrp,
                                           fchunk, sred, a.rowptr, a.colind, a.v32, steps,
                                           a.sys_of_tile, fs, nullptr, a.st.active);
                     __syncthreads();

@@ -147,6 +147,11 @@ struct StepArgs {
     int32_t pf_ahead;   // tiles ahead to prefetch into L2 (set by launch_step)
 };
 
+// Systems of at most DIRECT_MAX_N rows take the direct-read variant of the
+// step (one row per thread, no staging round: latency, not bytes, sets the
+// time of a step that is a handful of CTAs); the results are identical.
+constexpr int32_t DIRECT_MAX_N = 32768;
+
 // launch one fused step; returns the number of blocks (= partial sums for
 // OP_RESID) or a negative status
 template <typename T>

@@ -340,6 +340,68 @@ k_spmv_step(const StepArgs<T> a) {
     }
 }
 
+// Small systems: the same step, one row per thread, the row's matrix entries
+// read straight into registers (up to DIRECT_PRE of them) before the wait on
+// the previous step -- no shared-memory staging round, so the latency chain
+// of a step is row pointers -> (wait) -> gathers -> epilogue.  For a few
+// thousand rows a step is a handful of CTAs and that latency, not bytes,
+// sets its time.  Each row is summed in stored order with one FMA per
+// nonzero and the same epilogue as k_spmv_step: bit-identical results.
+constexpr int DIRECT_PRE = 8;
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(SPMV_ROWS)
+k_spmv_direct(const StepArgs<T> a) {
+    __shared__ double sred[SPMV_ROWS / 32];
+    const int tid = threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * SPMV_ROWS + tid;
+    const bool live = r < a.n;
+    asm volatile("griddepcontrol.launch_dependents;");
+    int32_t k0 = 0, k1 = 0;
+    T pv[DIRECT_PRE];
+    int32_t pc[DIRECT_PRE];
+    if (live) {
+        k0 = __ldg(a.rowptr + r);
+        k1 = __ldg(a.rowptr + r + 1);
+#pragma unroll
+        for (int q = 0; q < DIRECT_PRE; ++q) {
+            if (k0 + q < k1) {
+                pv[q] = __ldg(a.vals + k0 + q);
+                pc[q] = __ldg(a.colind + k0 + q);
+            }
+        }
+    }
+    // the vectors written by the previous step are complete and visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    double sq = 0.0;
+    if (live) {
+        const T e0 = a.a0 ? __ldg(a.a0 + r) : T(0);
+        const T e1 = (a.a1 && !(a.flags & F_PZERO)) ? a.a1[r] : T(0);
+        const T e2 = (a.a2 && (a.flags & F_FINAL)) ? __ldg(a.a2 + r) : T(0);
+        T xg[DIRECT_PRE];
+#pragma unroll
+        for (int q = 0; q < DIRECT_PRE; ++q)
+            if (k0 + q < k1) xg[q] = __ldg(a.x + pc[q]);
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < DIRECT_PRE; ++q)
+            if (k0 + q < k1) acc = fma(pv[q], xg[q], acc);
+        for (int32_t k = k0 + DIRECT_PRE; k < k1; ++k)
+            acc = fma(__ldg(a.vals + k), __ldg(a.x + __ldg(a.colind + k)), acc);
+        step_epilogue<T, OP>(a, r, acc, e0, e1, e2, sq);
+    }
+    if constexpr (OP == OP_RESID) {
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+        if ((tid & 31) == 0) sred[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < SPMV_ROWS / 32; ++w) t += sred[w];
+            a.part[blockIdx.x] = t;
+        }
+    }
+}
+
 // A root step whose operator product s = (M x)[r] was computed beforehand
 // (M a composite operator such as phi_1(A)): the same epilogue as the
 // fused kernel, one thread per row.
@@ -512,6 +574,28 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (op < OP_SPMV || op > OP_P_PAIR2) return PPG_ERR_ARG;
+    if (a_in.n <= DIRECT_MAX_N) {
+        // small system: one row per thread, no staging round
+        const int dgrid = (int)(((int64_t)a_in.n + SPMV_ROWS - 1) / SPMV_ROWS);
+        cfg.gridDim = dim3(dgrid);
+        cudaError_t ed;
+        switch (op) {
+            case OP_SPMV: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_SPMV>, a); break;
+            case OP_RESID: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_RESID>, a); break;
+            case OP_PHI_REAL: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_REAL>, a); break;
+            case OP_PHI_PAIR2: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_PAIR2>, a); break;
+            case OP_P_REAL: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_REAL>, a); break;
+            case OP_P_PAIR1: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR1>, a); break;
+            default: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR2>, a); break;
+        }
+        ++g_launches;
+        if (ed != cudaSuccess) {
+            set_cuda_error(ed, "cudaLaunchKernelEx(k_spmv_direct)");
+            return PPG_ERR_CUDA;
+        }
+        const int32_t rcd = check_launch("k_spmv_direct");
+        return rcd < 0 ? rcd : dgrid;
+    }
     const cudaError_t e =
         a.pf_ahead > 0 ? launch_op<T, true>(cfg, op, a) : launch_op<T, false>(cfg, op, a);
     ++g_launches;
