@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
     int32_t* fsrp = srp + group * (rows + 1);
     double* dsval = reinterpret_cast<double*>(sraw);
     int32_t* dscol = reinterpret_cast<int32_t*>(sraw + BCHUNK * 8);
-    const int64_t nvb_f = a.N / 256;   // CTA iterations of a root step: `groups` tiles each
+    const int64_t nvt_f = a.N / rows;   // tiles of `rows` rows in the batch
     int cycles = 0;
     for (int cyc = 0; cyc < a.max_cycles; ++cyc) {
         if (!any_active(a.st.active, nsolve)) break;
@@ -810,12 +810,13 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
             fs.p[B_C] = a.fc;
             for (int k = 0; k < a.K; ++k) {
                 const BStep* steps = a.steps_p + (size_t)k * a.nsys;
-                for (int64_t vb = blockIdx.x; vb < nvb_f; vb += gridDim.x) {
-                    bstep_tile<float, NR>(vb * groups + group, rows, gt, group, fsval, fscol, fsrp,
-                                          fchunk, sred, a.rowptr, a.colind, a.v32, steps,
-                                          a.sys_of_tile, fs, nullptr, a.st.active);
-                    __syncthreads();
-                }
+                // each row group strides over the tiles on its own: the groups use
+                // disjoint shared-memory slices and their own barriers
+                for (int64_t vt = (int64_t)blockIdx.x * groups + group; vt < nvt_f;
+                     vt += (int64_t)gridDim.x * groups)
+                    bstep_tile<float, NR>(vt, rows, gt, group, fsval, fscol, fsrp, fchunk, sred,
+                                          a.rowptr, a.colind, a.v32, steps, a.sys_of_tile, fs,
+                                          nullptr, a.st.active);
                 PSYNC();
             }
             for (int64_t e = gtid; e < total; e += gstride) a.zd[e] = (double)zj[e];
