@@ -379,17 +379,34 @@ __device__ __forceinline__ void bsub_block(int unit, double (*sh)[NR], double (*
     double nacc = 0.0;
     for (int t = t0; t < t1; ++t) {
         const int64_t base = (int64_t)t * BT;
+        // the NR rows of this thread in the tile share each coefficient load:
+        // column pairs outermost (even columns into s0, odd into s1, as a
+        // per-row loop would sum them), the rows innermost
+        const int64_t idx0 = (base + tid / NR) * NR + k;
+        double s0[NR], s1[NR];
+#pragma unroll
+        for (int p = 0; p < NR; ++p) s0[p] = s1[p] = 0.0;
+        int c = 0;
+        for (; c + 1 < ncol; c += 2) {
+            const double h0 = sh[c][k], h1 = sh[c + 1][k];
+            const double* v0 = V + c * ldV + idx0;
+            const double* v1 = V + (c + 1) * ldV + idx0;
+#pragma unroll
+            for (int p = 0; p < NR; ++p) {
+                s0[p] = fma(__ldcs(v0 + p * RP * NR), h0, s0[p]);
+                s1[p] = fma(__ldcs(v1 + p * RP * NR), h1, s1[p]);
+            }
+        }
+        if (c < ncol) {
+            const double h0 = sh[c][k];
+            const double* v0 = V + c * ldV + idx0;
+#pragma unroll
+            for (int p = 0; p < NR; ++p) s0[p] = fma(__ldcs(v0 + p * RP * NR), h0, s0[p]);
+        }
 #pragma unroll
         for (int p = 0; p < NR; ++p) {
-            const int64_t idx = (base + p * RP + tid / NR) * NR + k;
-            double s0 = 0.0, s1 = 0.0;
-            int c = 0;
-            for (; c + 1 < ncol; c += 2) {
-                s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
-                s1 = fma(__ldcs(V + (c + 1) * ldV + idx), sh[c + 1][k], s1);
-            }
-            if (c < ncol) s0 = fma(__ldcs(V + c * ldV + idx), sh[c][k], s0);
-            const double wn = w[idx] - (s0 + s1);
+            const int64_t idx = idx0 + (int64_t)p * RP * NR;
+            const double wn = w[idx] - (s0[p] + s1[p]);
             w[idx] = wn;
             nacc = fma(wn, wn, nacc);
         }
