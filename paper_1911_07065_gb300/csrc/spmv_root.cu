@@ -30,8 +30,7 @@
 
 namespace ppg {
 
-constexpr int SPMV_ROWS = 256;      // rows per CTA = threads per CTA
-constexpr int SPMV_CHUNK = 2048;    // nonzeros staged per chunk
+constexpr int SPMV_ROWS = 256;      // threads per CTA
 
 __device__ __forceinline__ uint64_t l2_policy(int keep) {
     uint64_t p;
@@ -68,19 +67,18 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, uint64_
                  : "memory");
 }
 
-// Stage elements [c0, c1) of src into shared memory as dst[k - base].  With
-// V16, base = c0 rounded down to a multiple of 4 elements (16-byte aligned
-// for 4- and 8-byte elements); with V16 and src 16-byte aligned, the 16-byte granules
-// of [base, c1 rounded down to 4) move with one cp.async each (the few
-// elements before c0 come along) and the ragged end per element, so nothing
-// at or past c1 is read; otherwise every element of [c0, c1) is copied
-// alone.  dst holds c1 - base elements.
-template <typename E, bool V16>
+// Stage elements [c0, c1) of src into shared memory as dst[k - base], with
+// base = c0 rounded down to a multiple of 4 elements.  With src 16-byte
+// aligned, the 16-byte granules of [base, c1 rounded down to 4) move with one
+// cp.async each (the few elements before c0 come along) and the ragged end
+// per element, so nothing at or past c1 is read; otherwise every element of
+// [c0, c1) is copied alone.  dst (16-byte aligned) holds c1 - base elements.
+template <typename E>
 __device__ __forceinline__ void stage_async(E* dst, const E* src, int32_t base, int32_t c0,
                                             int32_t c1, int tid, int nthr, uint64_t pol) {
     constexpr int PER = 16 / (int)sizeof(E);
     int32_t t0 = c0;
-    if (V16 && ((uintptr_t)src & 15) == 0) {
+    if (((uintptr_t)src & 15) == 0) {
         const int32_t vend = c1 & ~3;
         const int32_t nvec = vend > base ? (vend - base) / PER : 0;
         for (int32_t q = tid; q < nvec; q += nthr) cp_async16(dst + q * PER, src + base + q * PER, pol);
@@ -89,22 +87,15 @@ __device__ __forceinline__ void stage_async(E* dst, const E* src, int32_t base, 
     for (int32_t k = t0 + tid; k < c1; k += nthr) cp_async<sizeof(E)>(dst + (k - base), src + k, pol);
 }
 
-// Stage a chunk of values and column indices: with V16 (FP64 values) by
-// 16-byte granules from base = c0 & ~3; otherwise one fused per-element
-// loop from base = c0 (measured faster in FP32).
-template <typename T, bool V16>
+// Stage a chunk of values and column indices by 16-byte granules from
+// base = c0 & ~3 (measured faster than per-element copies in both precisions:
+// FP64 2-D 1000^2 chains -2.6 %, 3-D 160^3 -5 %; FP32 3-D 160^3 chains -8 %).
+template <typename T>
 __device__ __forceinline__ void stage_chunk(T* sval, int32_t* scol, const T* vals,
                                             const int32_t* colind, int32_t base, int32_t c0,
                                             int32_t c1, int tid, int nthr, uint64_t pol) {
-    if constexpr (V16) {
-        stage_async<T, true>(sval, vals, base, c0, c1, tid, nthr, pol);
-        stage_async<int32_t, true>(scol, colind, base, c0, c1, tid, nthr, pol);
-    } else {
-        for (int32_t k = c0 + tid; k < c1; k += nthr) {
-            cp_async<sizeof(T)>(sval + (k - base), vals + k, pol);
-            cp_async<4>(scol + (k - base), colind + k, pol);
-        }
-    }
+    stage_async<T>(sval, vals, base, c0, c1, tid, nthr, pol);
+    stage_async<int32_t>(scol, colind, base, c0, c1, tid, nthr, pol);
 }
 
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -159,6 +150,18 @@ __device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T
 template <typename T>
 __host__ __device__ constexpr int step_rpt() { return sizeof(T) == 4 ? 2 : 1; }
 
+// Nonzeros staged per chunk: FP64 2048 (256 rows of up to 8); FP32 3584, so
+// that a tile of 512 rows of a 7-point stencil is one chunk and the CTA's
+// 30.7 KB of shared memory lets 7 CTAs share an SM (with 4096, 6 fit:
+// 3-D 160^3 FP32 chains 1 % slower).  Longer tiles take several chunks.
+template <typename T>
+__host__ __device__ constexpr int step_chunk() { return sizeof(T) == 4 ? 3584 : 2048; }
+
+// CTAs per SM the register budget must allow (FP32: 32 registers instead
+// of 40; FP64 already compiles to 32)
+template <typename T>
+__host__ __device__ constexpr int step_min_ctas() { return sizeof(T) == 4 ? 7 : 8; }
+
 // one row's multiply-adds over its staged nonzeros [lo, hi): four gathers in
 // flight, then the last 1-3 (FP32: issued together; FP64: one at a time)
 template <typename T, bool WIDE_TAIL>
@@ -196,19 +199,16 @@ __device__ __forceinline__ T row_dot(const T* sval, const int32_t* scol, const T
     return acc;
 }
 
-// PF: prefetch the tile one resident wave ahead into L2 (launched when the
-// matrix is not held in an L2 set-aside)
+// PF: prefetch the tile a.pf_ahead tiles ahead (half a resident wave) into
+// L2 (launched when the matrix is not held in an L2 set-aside)
 template <typename T, int OP, bool PF>
-__global__ void __launch_bounds__(SPMV_ROWS)
+__global__ void __launch_bounds__(SPMV_ROWS, step_min_ctas<T>())
 k_spmv_step(const StepArgs<T> a) {
-    // 16-byte staging copies from a chunk base rounded down to 4 elements:
-    // measured faster in FP64 (2-D 1000^2 chains -2.6 %, 3-D 160^3 -5 %),
-    // slower in FP32, which keeps per-element copies from the chunk start
-    constexpr bool V16 = sizeof(T) == 8;
-    constexpr int PAD = V16 ? 4 : 0;
+    // staging copies start at a chunk base rounded down to 4 elements
+    constexpr int PAD = 4;
     constexpr int RPT = step_rpt<T>();
     constexpr int ROWS = SPMV_ROWS * RPT;      // rows per CTA
-    constexpr int CHUNK = SPMV_CHUNK * RPT;    // nonzeros staged per chunk
+    constexpr int CHUNK = step_chunk<T>();     // nonzeros staged per chunk
     __shared__ __align__(16) T sval[CHUNK + PAD];
     __shared__ __align__(16) int32_t scol[CHUNK + PAD];
     __shared__ int32_t srp[ROWS + 1];
@@ -222,10 +222,10 @@ k_spmv_step(const StepArgs<T> a) {
     // now; everything up to griddepcontrol.wait reads only the matrix, which
     // no step writes, so it overlaps the previous step's tail.
     asm volatile("griddepcontrol.launch_dependents;");
-    // the tile that the CTA one resident wave later stages: its nonzero
-    // range is read now, beside this tile's row pointers.  CTAs of the last
-    // wave prefetch the matrix tiles of the next step's first wave instead
-    // (a chain's next step reads the same matrix).
+    // the tile that a CTA half a resident wave later stages: its nonzero
+    // range is read now, beside this tile's row pointers.  CTAs near the end
+    // of the grid prefetch the matrix tiles at the start of the next step
+    // instead (a chain's next step reads the same matrix).
     int64_t prow = row0 + (int64_t)a.pf_ahead * ROWS;
     const bool wrap = prow >= a.n;
     if (wrap) prow -= (int64_t)gridDim.x * ROWS;
@@ -249,15 +249,18 @@ k_spmv_step(const StepArgs<T> a) {
         my_hi[q] = (t < nrows) ? srp[t + 1] : k1;
     }
     // element k of the current chunk sits at sval / scol [k - base], base =
-    // c0 & ~3 with 16-byte copies, else c0
+    // c0 & ~3
     {
         const int32_t c1 = min(k1, k0 + CHUNK);
-        const int32_t base = V16 ? (k0 & ~3) : k0;
-        stage_chunk<T, V16>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS, pol);
+        const int32_t base = k0 & ~3;
+        stage_chunk<T>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS, pol);
     }
     if (pf) {
         prefetch_l2(a.vals + pk0, a.vals + pk1);
         prefetch_l2(a.colind + pk0, a.colind + pk1);
+        // and its row pointers, which the CTA reads first, before anything
+        // else can start (3-D 160^3 FP32 chains -4 %)
+        prefetch_l2(a.rowptr + prow, a.rowptr + prow1 + 1);
     }
     // the vectors written by the previous step are complete and visible
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -285,9 +288,9 @@ k_spmv_step(const StepArgs<T> a) {
 
     for (int32_t c0 = k0; c0 < k1; c0 += CHUNK) {
         const int32_t c1 = min(k1, c0 + CHUNK);
-        const int32_t base = V16 ? (c0 & ~3) : c0;
+        const int32_t base = c0 & ~3;
         if (c0 != k0) {   // the first chunk was issued before the wait
-            stage_chunk<T, V16>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS, pol);
+            stage_chunk<T>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS, pol);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -299,7 +302,7 @@ k_spmv_step(const StepArgs<T> a) {
         if constexpr (RPT == 1) {
             const int32_t lo = max(my_lo[0], c0) - base;
             const int32_t hi = min(my_hi[0], c1) - base;
-            acc[0] = row_dot<T, !V16>(sval, scol, a.x, lo, hi, acc[0]);
+            acc[0] = row_dot<T, sizeof(T) == 4>(sval, scol, a.x, lo, hi, acc[0]);
         } else {
             // two rows: their four-wide batches in lockstep (eight gathers
             // in flight), then each row's remainder
@@ -560,9 +563,12 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     const int rows = SPMV_ROWS * step_rpt<T>();
     const int grid = (int)(((int64_t)a_in.n + rows - 1) / rows);
     StepArgs<T> a = a_in;
-    // prefetch ahead by one resident wave, unless the matrix is held in an
-    // L2 set-aside (measured: the prefetches then cost more than they save)
-    a.pf_ahead = (a.flags & F_KEEP_A) ? 0 : step_resident_ctas<T>();
+    // prefetch half a resident wave ahead, unless the matrix is held in an
+    // L2 set-aside (measured: the prefetches then cost more than they save).
+    // 3-D 160^3 chains (FP32 / FP64) by distance in resident waves:
+    // 1/4 5860 / 6121 GB/s, 1/3 6017 / 6141, 1/2 6041 / 6151, 1 5969 / 6142,
+    // 3/2 5836 / 6123, 2 5218 / 5982.
+    a.pf_ahead = (a.flags & F_KEEP_A) ? 0 : (step_resident_ctas<T>() + 1) / 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(SPMV_ROWS);
