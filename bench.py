@@ -772,8 +772,10 @@ def run_profile_case(name):
     (n = 4e6, FP64; the matrix and vectors exceed L2), six real roots;
     ``arnoldi_cd2d_2000``: the degree-30 polynomial construction on it (CGS2);
     ``phi_cd2d_1000``: two applications of the benchmark's own polynomial;
-    ``batched_64x4``: one call of the batching form on its full workload;
-    ``batched_16x4``: the same with its first 16 systems;
+    ``batched_64x4``: one call of the batching form on its full workload
+    (the persistent launch); ``batched_16x4``: the same with its first 16
+    systems; ``batched_64x4_graph`` / ``batched_16x4_graph``: the same calls
+    with one CUDA graph per restart cycle (the per-phase kernels);
     ``p_cd3d_160_f32``: Algorithm 3 in FP32 on the 160^3 matrix;
     ``sweep_p_cd3d_160_f32``: the same through a fused-sweep plan;
     ``chain_phi_cd3d_160_f64`` / ``chain_p_cd3d_160_f32``: the 160^3 workload's
@@ -801,17 +803,18 @@ def run_profile_case(name):
         v = torch.from_numpy(np.random.default_rng(0).standard_normal(A.n)).cuda()
         y = ppg.apply_phi(Ad, R, v)
         y = ppg.apply_phi(Ad, R, y)
-    elif name in ("batched_64x4", "batched_16x4"):
+    elif name in ("batched_64x4", "batched_16x4", "batched_64x4_graph", "batched_16x4_graph"):
         # the batching workload: 64 systems x 4 right-hand sides, one call;
         # batched_16x4: its first 16 systems (same recipe; about 2 GB on the
         # device, for full ncu captures)
-        probs = synth.batch_problem(nsys=64 if name == "batched_64x4" else 16, seed=104)
+        probs = synth.batch_problem(nsys=64 if name.startswith("batched_64x4") else 16, seed=104)
         dA = [ppg.CSR.from_host(A.rowptr, A.colind, A.vals) for A, _, _ in probs]
         dB = [torch.from_numpy(np.ascontiguousarray(B)).cuda() for _, B, _ in probs]
         dv = [torch.from_numpy(v).cuda() for _, _, v in probs]
         side = torch.cuda.Stream()
         with torch.cuda.stream(side):
-            Xs, _ = ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10)
+            Xs, _ = ppg.solve_batched(dA, dB, dv, 20, 30, 1e-10,
+                                      persistent=not name.endswith("_graph"))
         torch.cuda.synchronize()
         A = probs[0][0]
         y = Xs[0]

@@ -1135,7 +1135,11 @@ int32_t run_persistent(const Batch& B, Work& W, int K, double tol, int max_cycle
     a.ldh = B.ldh;
     a.K = K;
     a.max_cycles = max_cycles;
-    a.rows = B.rows_per_cta;
+    // FP32 root steps on row groups of 64 rows, four per CTA (whole 64 x 4
+    // batching call: 64 rows 1.32 s, 128 rows 1.33 s, 256 rows 1.37 s; the
+    // per-cycle graph's tuned kernel prefers 256: 1.22 s against 1.30 s and
+    // 1.51 s)
+    a.rows = 64;
     a.N = B.N;
     a.nunits = B.nunits;
     a.ntiles = B.ntiles;
