@@ -139,7 +139,8 @@ static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const in
                          const Buffers& bufs, cudaStream_t s, double* bytes_out,
                          bool reserve_l2) {
     double bytes = 0.0;
-    const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3, reserve_l2);
+    int32_t keep_rows = 0;
+    const int keep = keep_a_flag(n, nnz, (int)sizeof(T), 3, reserve_l2, &keep_rows);
     for (int i = i0; i < i1; ++i) {
         const Step& st = plan[(size_t)i];
         if (st.op == OP_AXPY) {
@@ -149,7 +150,7 @@ static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const in
             bytes += (double)sizeof(T) * n * (pz ? 2 : 3);
             continue;
         }
-        StepArgs<T> a;
+        StepArgs<T> a{};
         a.rowptr = rowptr;
         a.colind = colind;
         a.vals = vals;
@@ -164,6 +165,7 @@ static int32_t run_steps(const std::vector<Step>& plan, int i0, int i1, const in
         a.c2 = (T)st.c2;
         a.c3 = (T)st.c3;
         a.flags = st.flags | keep;
+        a.keep_rows = keep_rows;
         a.part = nullptr;
         int32_t rc = launch_step<T>(st.op, a, s);
         if (rc < 0) return rc;

@@ -145,6 +145,9 @@ struct StepArgs {
     int32_t flags;
     double* part;
     int32_t pf_ahead;   // tiles ahead to prefetch into L2 (set by launch_step)
+    int32_t keep_rows;  // rows [0, keep_rows) stage their nonzeros with an L2
+                        // evict-last hint (a chain over a matrix too large
+                        // for L2 keeps its leading rows resident)
 };
 
 // Systems of at most DIRECT_MAX_N rows take the direct-read variant of the
@@ -167,7 +170,13 @@ int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_
 // the process's context on the current device); with may_reserve = false
 // nothing is reserved and F_KEEP_A is returned only if a set-aside large
 // enough already exists on this device.
-int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve = true);
+// keep_rows (root-step chains only): for a matrix that does not fit, the
+// number of leading rows whose nonzeros a chain holds in an L2 set-aside of
+// about 48 MB, which is set to that size (with may_reserve; otherwise the
+// set-aside in place, if any, is used); 0 without a set-aside.  Other callers
+// pass nullptr and leave the set-aside as it is.
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve = true,
+                int32_t* keep_rows = nullptr);
 
 int32_t spmv_grid_blocks(int32_t n);
 

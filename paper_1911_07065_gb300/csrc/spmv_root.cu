@@ -158,9 +158,13 @@ template <typename T>
 __host__ __device__ constexpr int step_chunk() { return sizeof(T) == 4 ? 3584 : 2048; }
 
 // CTAs per SM the register budget must allow (FP32: 32 registers instead
-// of 40; FP64 already compiles to 32)
-template <typename T>
-__host__ __device__ constexpr int step_min_ctas() { return sizeof(T) == 4 ? 7 : 8; }
+// of 40; FP64 already compiles to 32).  The FP32 second step of a pair of
+// Algorithm 1 (not on the precision form's path, which applies p(A) only)
+// keeps 40 registers and 6 CTAs: at 32 it spills.
+template <typename T, int OP>
+__host__ __device__ constexpr int step_min_ctas() {
+    return sizeof(T) == 4 ? (OP == OP_PHI_PAIR2 ? 6 : 7) : 8;
+}
 
 // one row's multiply-adds over its staged nonzeros [lo, hi): four gathers in
 // flight, then the last 1-3 (FP32: issued together; FP64: one at a time)
@@ -202,7 +206,7 @@ __device__ __forceinline__ T row_dot(const T* sval, const int32_t* scol, const T
 // PF: prefetch the tile a.pf_ahead tiles ahead (half a resident wave) into
 // L2 (launched when the matrix is not held in an L2 set-aside)
 template <typename T, int OP, bool PF>
-__global__ void __launch_bounds__(SPMV_ROWS, step_min_ctas<T>())
+__global__ void __launch_bounds__(SPMV_ROWS, step_min_ctas<T, OP>())
 k_spmv_step(const StepArgs<T> a) {
     // staging copies start at a chunk base rounded down to 4 elements
     constexpr int PAD = 4;
@@ -217,7 +221,10 @@ k_spmv_step(const StepArgs<T> a) {
     const int64_t row0 = (int64_t)blockIdx.x * ROWS;
     const int tid = threadIdx.x;
     const int nrows = (int)(((int64_t)a.n - row0) < ROWS ? ((int64_t)a.n - row0) : ROWS);
-    const uint64_t pol = l2_policy(a.flags & F_KEEP_A);
+    // L2 hint of the staging copies: evict-last for a matrix held in L2 (all
+    // of it, or the leading rows), else evict-first (the policy is created
+    // at each use, so that it holds no registers across the kernel)
+    const bool keep = (a.flags & F_KEEP_A) || row0 < a.keep_rows;
     // Programmatic dependent launch: the next step in the stream may start
     // now; everything up to griddepcontrol.wait reads only the matrix, which
     // no step writes, so it overlaps the previous step's tail.
@@ -253,11 +260,14 @@ k_spmv_step(const StepArgs<T> a) {
     {
         const int32_t c1 = min(k1, k0 + CHUNK);
         const int32_t base = k0 & ~3;
-        stage_chunk<T>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS, pol);
+        stage_chunk<T>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS,
+                       l2_policy(keep));
     }
     if (pf) {
-        prefetch_l2(a.vals + pk0, a.vals + pk1);
-        prefetch_l2(a.colind + pk0, a.colind + pk1);
+        if (prow >= a.keep_rows) {   // (the leading rows' nonzeros are held in L2)
+            prefetch_l2(a.vals + pk0, a.vals + pk1);
+            prefetch_l2(a.colind + pk0, a.colind + pk1);
+        }
         // and its row pointers, which the CTA reads first, before anything
         // else can start (3-D 160^3 FP32 chains -4 %)
         prefetch_l2(a.rowptr + prow, a.rowptr + prow1 + 1);
@@ -290,7 +300,8 @@ k_spmv_step(const StepArgs<T> a) {
         const int32_t c1 = min(k1, c0 + CHUNK);
         const int32_t base = c0 & ~3;
         if (c0 != k0) {   // the first chunk was issued before the wait
-            stage_chunk<T>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS, pol);
+            stage_chunk<T>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS,
+                           l2_policy(keep));
         }
         cp_async_wait_all();
         __syncthreads();
@@ -459,10 +470,12 @@ int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
 
 // Reserve L2 for evict-last (persisting) lines on the current device: without
 // a set-aside the evict-last hint is treated as normal.  This is a limit of
-// this process's context on that device; it ends with the process.  Returns
-// the set-aside now in place.
+// this process's context on that device; it ends with the process.  A
+// chain over a matrix too large for L2 sets it to kPartialL2 instead
+// (set_l2_exact).  Returns the set-aside now in place.
 constexpr int kL2Devices = 64;
-static std::atomic<size_t> g_l2_reserved[kL2Devices];
+static std::atomic<size_t> g_l2_reserved[kL2Devices];   // set-aside in place
+static std::atomic<size_t> g_l2_asked[kL2Devices];      // what set_l2_exact asked for
 static std::atomic<int> g_l2_bytes[kL2Devices];
 
 static int current_device() {
@@ -484,16 +497,49 @@ static size_t reserve_l2_for(int dev, size_t bytes) {
         return have;
     }
     const size_t want = bytes < (size_t)maxp ? bytes : (size_t)maxp;
-    if (want > have && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) {
-        g_l2_reserved[dev].store(want, std::memory_order_relaxed);
-        cudaGetLastError();
-        return want;
+    size_t got = have;
+    if (want > have && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess &&
+        cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+        g_l2_reserved[dev].store(got, std::memory_order_relaxed);
+        g_l2_asked[dev].store(0, std::memory_order_relaxed);
     }
     cudaGetLastError();
-    return have;
+    return g_l2_reserved[dev].load(std::memory_order_relaxed);
 }
 
-int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve) {
+// Set the set-aside to `bytes` exactly (shrinking or growing it; persisting
+// lines back to normal first).  Returns the set-aside now in place (the
+// driver rounds the request to its granularity).
+static size_t set_l2_exact(int dev, size_t bytes) {
+    const size_t have = g_l2_reserved[dev].load(std::memory_order_relaxed);
+    if (g_l2_asked[dev].load(std::memory_order_relaxed) == bytes) return have;
+    int maxp = 0;
+    if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        maxp <= 0) {
+        cudaGetLastError();
+        return have;
+    }
+    const size_t want = bytes < (size_t)maxp ? bytes : (size_t)maxp;
+    cudaCtxResetPersistingL2Cache();
+    size_t got = have;
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess &&
+        cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize) == cudaSuccess) {
+        g_l2_reserved[dev].store(got, std::memory_order_relaxed);
+        g_l2_asked[dev].store(bytes, std::memory_order_relaxed);
+    }
+    cudaGetLastError();
+    return g_l2_reserved[dev].load(std::memory_order_relaxed);
+}
+
+// Set-aside a chain over a matrix too large for L2 holds its leading rows in.
+// Measured on the 3-D 160^3 chains with an unused set-aside (FP32 / FP64
+// GB/s): none 6032 / 6150, 48 MB 6018 / 6147, 67 MB 5357 / 6032, 80 MB
+// 4646 / 5604: up to about 48 MB the streamed part loses next to nothing.
+constexpr size_t kPartialL2 = (size_t)48 << 20;
+
+int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve,
+                int32_t* keep_rows) {
+    if (keep_rows) *keep_rows = 0;
     const int dev = current_device();
     if (dev < 0) return 0;
     int l2 = g_l2_bytes[dev].load(std::memory_order_relaxed);
@@ -506,10 +552,21 @@ int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve) {
         g_l2_bytes[dev].store(v, std::memory_order_relaxed);
         l2 = v;
     }
-    if (l2 <= 0) return 0;
+    if (l2 <= 0 || n <= 0) return 0;
     const double a_bytes = (double)nnz * (elem + 4) + 4.0 * (n + 1);
     const double bytes = a_bytes + (double)nvec * n * elem;
-    if (!(bytes <= 0.8 * (double)l2)) return 0;
+    if (!(bytes <= 0.8 * (double)l2)) {
+        // streaming: a chain holds the nonzeros of its leading rows in a
+        // set-aside of kPartialL2 (shrinking a larger one that an L2-resident
+        // workload left: an unused 76 MB set-aside cost the 160^3 FP32 chains
+        // 11 %), and streams the rest
+        if (!keep_rows) return 0;
+        const size_t have = may_reserve ? set_l2_exact(dev, kPartialL2)
+                                        : g_l2_reserved[dev].load(std::memory_order_relaxed);
+        const double rows = 0.9 * (double)have / (a_bytes / (double)n);
+        *keep_rows = (int32_t)(rows < (double)n ? rows : (double)n);
+        return 0;
+    }
     const size_t need = (size_t)(a_bytes * 1.05);
     if (may_reserve) {
         reserve_l2_for(dev, need);

@@ -39,7 +39,9 @@ def p_norm_estimate(apply_fn, apply_t_fn, n, iters=30, seed=0):
 
 def random_csr(n, seed, max_row=12, long_rows=(), empty_rows=(), diag=4.0):
     """Random sparse matrix with variable row lengths, optional long rows
-    (more nonzeros than one staging chunk) and empty rows."""
+    (more nonzeros than one staging chunk) and empty rows.  Above 5000 rows
+    the columns of a row are drawn with replacement and deduplicated (a row
+    may then hold fewer than its drawn length)."""
     rng = np.random.default_rng(seed)
     rows = []
     for i in range(n):
@@ -47,7 +49,10 @@ def random_csr(n, seed, max_row=12, long_rows=(), empty_rows=(), diag=4.0):
             rows.append(np.zeros(0, dtype=np.int64))
             continue
         k = int(long_rows[i]) if i in long_rows else int(rng.integers(1, max_row + 1))
-        cols = rng.choice(n, size=min(k, n), replace=False)
+        if n > 5000:
+            cols = rng.integers(0, n, size=min(k, n))
+        else:
+            cols = rng.choice(n, size=min(k, n), replace=False)
         cols = np.unique(np.concatenate([cols, [i]]))
         rows.append(cols)
     rowptr = np.zeros(n + 1, dtype=np.int64)

@@ -1,8 +1,9 @@
 """Edge cases of the device path (run with -m gpu).
 
 * CSR arrays that do not start on a 16-byte boundary (views one element into
-  a buffer): the root-step kernels then stage values and column indices one
-  element at a time instead of in 16-byte granules.  Staging only moves data,
+  a buffer): the staged root-step kernel (systems above 32,768 rows) then
+  stages values and column indices one element at a time instead of in
+  16-byte granules.  Staging only moves data,
   so y = A x, p(A) v and phi(A) v must be bit-identical to the aligned run,
   in FP64 and FP32, including matrices with rows longer than one staging
   chunk and empty rows.
@@ -44,10 +45,17 @@ def _unaligned(torch, t, offset=1):
 
 
 def _matrices():
+    # at most 32,768 rows: the direct kernel (no staging; alignment must not
+    # matter either); above: the staged kernel, whose copies fall back to
+    # one element at a time for arrays off a 16-byte boundary
     yield "cd2d_37", synth.cd2d(37, 0.7)
     yield "cd3d_13", synth.cd3d(13, (0.8, 0.4, 0.2))
     yield "random_long_empty", random_csr(3001, 1, long_rows={5: 2500, 700: 4100},
                                           empty_rows={17, 1000, 3000})
+    yield "cd3d_34", synth.cd3d(34, (0.8, 0.4, 0.2))
+    yield "random_long_empty_40k", random_csr(40001, 3, long_rows={5: 2500, 700: 4100,
+                                                                   33000: 9000},
+                                              empty_rows={17, 1000, 40000})
 
 
 @pytest.mark.parametrize("which", ["vals", "colind", "both"])

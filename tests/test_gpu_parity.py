@@ -1,5 +1,12 @@
 """GPU-vs-oracle parity through the C ABI (run with -m gpu).
 
+Systems of at most 32,768 rows run the direct root-step kernel (one row per
+thread, no staging); larger ones the staged, tiled kernel.  The matrices
+below cover both: small stencils and a random matrix with long and empty
+rows, and stencils and a random matrix of 36,100-40,001 rows (ragged last
+tiles; the random one with rows longer than a staging chunk, and in FP32
+most of its 512-row tiles in several chunks).
+
 Tolerances (FP64): SpMV within 1e-15 of the row's absolute sum; p(A) v and
 phi(A) v within 1e-11 ||p(A)||_2 ||v|| in norm and per element; Hbar within
 1e-10 relative; roots within 1e-10 max(1, kappa_i); solve: true residual
@@ -44,7 +51,19 @@ def _matrices():
                                           empty_rows={17, 1000, 3000})
 
 
-@pytest.mark.parametrize("mname,A", list(_matrices()))
+def _large_matrices():
+    # staged kernel: 36100 = 141 * 256 + 4 rows, 39304 = 76 * 512 + 392
+    yield "cd2d_190", synth.cd2d(190, 0.7)
+    yield "cd3d_34", synth.cd3d(34, (0.8, 0.4, 0.2))
+
+
+def _large_random():
+    return random_csr(40001, 3, long_rows={5: 2500, 700: 4100, 33000: 9000},
+                      empty_rows={17, 1000, 40000})
+
+
+@pytest.mark.parametrize("mname,A", list(_matrices()) + list(_large_matrices())
+                         + [("random_long_empty_40k", _large_random())])
 def test_spmv_matches_oracle(env, mname, A):
     p, torch = env
     As = A.to_scipy()
@@ -61,7 +80,7 @@ def _scaled_err(y, ref, pnorm, v):
 
 
 @pytest.mark.parametrize("rname", list(ROOT_SETS))
-@pytest.mark.parametrize("mname,A", list(_matrices())[:2])
+@pytest.mark.parametrize("mname,A", list(_matrices())[:2] + list(_large_matrices()))
 def test_apply_p_and_phi_fp64_match_oracle(env, rname, mname, A):
     p, torch = env
     roots = ROOT_SETS[rname]
@@ -84,11 +103,12 @@ def test_apply_p_and_phi_fp64_match_oracle(env, rname, mname, A):
     assert e2 <= 1e-11 and einf <= 1e-11
 
 
+@pytest.mark.parametrize("side", [13, 34])
 @pytest.mark.parametrize("rname", ["real", "ends_in_pair", "pair_then_real", "single_real"])
-def test_apply_p_fp32_matches_float32_oracle(env, rname):
+def test_apply_p_fp32_matches_float32_oracle(env, rname, side):
     p, torch = env
     roots = ROOT_SETS[rname]
-    A = synth.cd3d(13, (0.8, 0.4, 0.2))
+    A = synth.cd3d(side, (0.8, 0.4, 0.2))
     As32 = A.to_scipy().astype(np.float32)
     Ad = dev_csr(p, torch, A, dtype=torch.float32)
     R = p.Roots.from_complex(roots)
@@ -106,15 +126,33 @@ def test_apply_p_fp32_matches_float32_oracle(env, rname):
     assert e2 <= 1e-5 and einf <= 1e-5
 
 
-def test_apply_on_matrix_with_long_and_empty_rows(env):
+@pytest.mark.parametrize("n", [3001, 40001])
+def test_apply_on_matrix_with_long_and_empty_rows(env, n):
     p, torch = env
-    A = random_csr(3001, 2, long_rows={5: 2500, 700: 4100}, empty_rows={17, 1000, 3000})
+    if n == 3001:
+        A = random_csr(3001, 2, long_rows={5: 2500, 700: 4100}, empty_rows={17, 1000, 3000})
+    else:
+        A = _large_random()
     As = A.to_scipy()
     roots = ROOT_SETS["ends_in_pair"] * 2.0
+    R = p.Roots.from_complex(roots)
     v = np.random.default_rng(6).standard_normal(A.n)
-    y = p.apply_poly(dev_csr(p, torch, A), p.Roots.from_complex(roots), to_dev(torch, v))
+    y = p.apply_poly(dev_csr(p, torch, A), R, to_dev(torch, v))
     ref = poly.apply_p(As, roots, v)
     assert np.linalg.norm(y.cpu().numpy() - ref) <= 1e-11 * np.linalg.norm(ref) * 10
+    yf = p.apply_phi(dev_csr(p, torch, A), R, to_dev(torch, v))
+    reff = poly.apply_phi(As, roots, v)
+    assert np.linalg.norm(yf.cpu().numpy() - reff) <= 1e-11 * np.linalg.norm(reff) * 10
+    # FP32: as accurate as the oracle's float32 Algorithm 3 on the same data
+    As32 = As.astype(np.float32)
+    v32 = v.astype(np.float32)
+    y32 = p.apply_poly(dev_csr(p, torch, A, dtype=torch.float32), R,
+                       to_dev(torch, v32, torch.float32)).cpu().numpy().astype(np.float64)
+    r32 = gmres.apply_p32(As32, gmres._roots32(roots), v32).astype(np.float64)
+    r64 = poly.apply_p(As, roots, v32.astype(np.float64))
+    e_orc = np.linalg.norm(r32 - r64)
+    assert np.linalg.norm(y32 - r64) <= 3.0 * e_orc
+    assert np.linalg.norm(y32 - r32) <= 4.0 * e_orc
 
 
 def test_build_poly_matches_oracle_hbar_and_roots(env):
