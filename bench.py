@@ -432,7 +432,9 @@ def run_ours(args, rank, local, world):
                                "spmv_root_chains": round(st["poly_ms"], 3),
                                "cgs2_givens": round(st["ortho_ms"], 3)},
         "true_relres": rel, "converged": bool(st["converged"]),
-        "roofline": {"bound": "hbm", "kernel": "k_spmv_step (fused SpMV-root, Alg 1/3)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_spmv_direct (fused SpMV-root, Alg 1/3; the matrix held in L2, "
+                               "read directly)",
                      "achieved": round(achieved, 1) if achieved else None,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if achieved else None,

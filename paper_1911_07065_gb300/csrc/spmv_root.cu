@@ -354,17 +354,41 @@ k_spmv_step(const StepArgs<T> a) {
     }
 }
 
-// Small systems: the same step, one row per thread, the row's matrix entries
-// read straight into registers (up to DIRECT_PRE of them) before the wait on
-// the previous step -- no shared-memory staging round, so the latency chain
-// of a step is row pointers -> (wait) -> gathers -> epilogue.  For a few
-// thousand rows a step is a handful of CTAs and that latency, not bytes,
-// sets its time.  Each row is summed in stored order with one FMA per
-// nonzero and the same epilogue as k_spmv_step: bit-identical results.
-constexpr int DIRECT_PRE = 8;
+// Direct-read step: the same step, one row per thread, the row's matrix
+// entries read straight into registers (up to PRE of them) before the wait
+// on the previous step -- no shared-memory staging round, so the latency
+// chain of a step is row pointers -> (wait) -> gathers -> epilogue.  Each
+// row is summed in stored order with one FMA per nonzero and the same
+// epilogue as k_spmv_step: bit-identical results.  Two uses:
+// * small systems (PRE = 8, no register bound): a step is a handful of CTAs,
+//   and latency, not bytes, sets its time;
+// * a matrix held in L2 (F_KEEP_A; PRE = 3 or 4 and 32 registers, 8 CTAs
+//   per SM; the preloads carry the evict-last hint): the staging round trip
+//   is then the longer path.  2-D 1000^2 FP64 chains 57.3 -> 55.2 ms.
+// MINB: minimum CTAs per SM given to __launch_bounds__ (0: no register bound).
+template <typename T>
+__device__ __forceinline__ T ld_hint(const T* p, uint64_t pol);
+template <>
+__device__ __forceinline__ double ld_hint<double>(const double* p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <>
+__device__ __forceinline__ float ld_hint<float>(const float* p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <>
+__device__ __forceinline__ int32_t ld_hint<int32_t>(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(SPMV_ROWS)
+template <typename T, int OP, int PRE, int MINB, bool HINT>
+__global__ void __launch_bounds__(SPMV_ROWS, MINB)
 k_spmv_direct(const StepArgs<T> a) {
     __shared__ double sred[SPMV_ROWS / 32];
     const int tid = threadIdx.x;
@@ -372,16 +396,21 @@ k_spmv_direct(const StepArgs<T> a) {
     const bool live = r < a.n;
     asm volatile("griddepcontrol.launch_dependents;");
     int32_t k0 = 0, k1 = 0;
-    T pv[DIRECT_PRE];
-    int32_t pc[DIRECT_PRE];
+    T pv[PRE];
+    int32_t pc[PRE];
     if (live) {
         k0 = __ldg(a.rowptr + r);
         k1 = __ldg(a.rowptr + r + 1);
 #pragma unroll
-        for (int q = 0; q < DIRECT_PRE; ++q) {
+        for (int q = 0; q < PRE; ++q) {
             if (k0 + q < k1) {
-                pv[q] = __ldg(a.vals + k0 + q);
-                pc[q] = __ldg(a.colind + k0 + q);
+                if constexpr (HINT) {
+                    pv[q] = ld_hint<T>(a.vals + k0 + q, l2_policy(1));
+                    pc[q] = ld_hint<int32_t>(a.colind + k0 + q, l2_policy(1));
+                } else {
+                    pv[q] = __ldg(a.vals + k0 + q);
+                    pc[q] = __ldg(a.colind + k0 + q);
+                }
             }
         }
     }
@@ -392,15 +421,17 @@ k_spmv_direct(const StepArgs<T> a) {
         const T e0 = a.a0 ? __ldg(a.a0 + r) : T(0);
         const T e1 = (a.a1 && !(a.flags & F_PZERO)) ? a.a1[r] : T(0);
         const T e2 = (a.a2 && (a.flags & F_FINAL)) ? __ldg(a.a2 + r) : T(0);
-        T xg[DIRECT_PRE];
+        T xg[PRE];
 #pragma unroll
-        for (int q = 0; q < DIRECT_PRE; ++q)
+        for (int q = 0; q < PRE; ++q)
             if (k0 + q < k1) xg[q] = __ldg(a.x + pc[q]);
         T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < DIRECT_PRE; ++q)
+        for (int q = 0; q < PRE; ++q)
             if (k0 + q < k1) acc = fma(pv[q], xg[q], acc);
-        for (int32_t k = k0 + DIRECT_PRE; k < k1; ++k)
+        // (entries past PRE without the hint: mostly in the lines the hinted
+        // loads already brought in)
+        for (int32_t k = k0 + PRE; k < k1; ++k)
             acc = fma(__ldg(a.vals + k), __ldg(a.x + __ldg(a.colind + k)), acc);
         step_epilogue<T, OP>(a, r, acc, e0, e1, e2, sq);
     }
@@ -600,6 +631,25 @@ static int step_resident_ctas() {
     return v;
 }
 
+template <typename T, int PRE, int MINB, bool HINT>
+static cudaError_t launch_direct(cudaLaunchConfig_t& cfg, int op, const StepArgs<T>& a) {
+    switch (op) {
+        case OP_SPMV: return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_SPMV, PRE, MINB, HINT>, a);
+        case OP_RESID: return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_RESID, PRE, MINB, HINT>, a);
+        case OP_PHI_REAL:
+            return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_REAL, PRE, MINB, HINT>, a);
+        case OP_PHI_PAIR2:
+            return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_PAIR2, PRE, MINB, HINT>, a);
+        case OP_P_REAL:
+            return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_REAL, PRE, MINB, HINT>, a);
+        case OP_P_PAIR1:
+            return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR1, PRE, MINB, HINT>, a);
+        case OP_P_PAIR2:
+            return cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR2, PRE, MINB, HINT>, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename T, bool PF>
 static cudaError_t launch_op(cudaLaunchConfig_t& cfg, int op, const StepArgs<T>& a) {
     switch (op) {
@@ -637,20 +687,24 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (op < OP_SPMV || op > OP_P_PAIR2) return PPG_ERR_ARG;
-    if (a_in.n <= DIRECT_MAX_N) {
-        // small system: one row per thread, no staging round
+    const bool small = a_in.n <= DIRECT_MAX_N;
+    if (small || (a_in.flags & F_KEEP_A)) {
+        // one row per thread, no staging round (small system, or matrix in L2)
         const int dgrid = (int)(((int64_t)a_in.n + SPMV_ROWS - 1) / SPMV_ROWS);
         cfg.gridDim = dim3(dgrid);
+        // matrix in L2: four entries preloaded at 32 registers (8 CTAs per SM),
+        // three for the second step of a pair of Algorithm 1, which spills at
+        // four (2-D 1000^2 FP64 chains: staged kernel 57.3 ms; direct with
+        // four preloads 55.8 ms (without the evict-last hint 56.3 ms); three for
+        // the pair step 55.2 ms; three everywhere 55.7; five at 40 registers
+        // 55.4)
         cudaError_t ed;
-        switch (op) {
-            case OP_SPMV: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_SPMV>, a); break;
-            case OP_RESID: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_RESID>, a); break;
-            case OP_PHI_REAL: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_REAL>, a); break;
-            case OP_PHI_PAIR2: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_PHI_PAIR2>, a); break;
-            case OP_P_REAL: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_REAL>, a); break;
-            case OP_P_PAIR1: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR1>, a); break;
-            default: ed = cudaLaunchKernelEx(&cfg, k_spmv_direct<T, OP_P_PAIR2>, a); break;
-        }
+        if (small)
+            ed = launch_direct<T, 8, 0, false>(cfg, op, a);
+        else if (op == OP_PHI_PAIR2)
+            ed = launch_direct<T, 3, 8, true>(cfg, op, a);
+        else
+            ed = launch_direct<T, 4, 8, true>(cfg, op, a);
         ++g_launches;
         if (ed != cudaSuccess) {
             set_cuda_error(ed, "cudaLaunchKernelEx(k_spmv_direct)");
