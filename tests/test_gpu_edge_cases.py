@@ -176,3 +176,41 @@ def test_empty_and_one_by_one_matrices(env, dtype):
             ref = gmres.apply_p32(As.astype(np.float32), gmres._roots32(ROOTS),
                                   v.astype(np.float32)).astype(np.float64)
             assert np.allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def _block_diag_with_identity(A, n_extra, scale=4.0):
+    """A (+) scale I: the first block's rows read only the first block's
+    entries of x, so they compute exactly what A alone computes."""
+    n = A.n + n_extra
+    rowptr = np.concatenate([A.rowptr, A.rowptr[-1] + np.arange(1, n_extra + 1)]).astype(np.int32)
+    colind = np.concatenate([A.colind, A.n + np.arange(n_extra)]).astype(np.int32)
+    vals = np.concatenate([A.vals, np.full(n_extra, scale)])
+    return synth.CSRHost(n, rowptr, colind, vals)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("side", [50, 128])
+def test_small_system_and_l2_resident_steps_are_bitwise(env, side, dtype):
+    """Systems of up to 32,768 rows run the direct-read step with eight
+    entries preloaded and no register bound; the same matrix as the first
+    block of a 70,000-row block-diagonal system (held in L2) runs the
+    direct-read step with three or four entries preloaded under a 32-register
+    bound.  p(A) v and phi(A) v on the first block must agree bit for bit,
+    for root sets with real roots, pairs and a final real root, and with a
+    degree-one polynomial."""
+    p, torch = env
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    A = synth.cd2d(side, 0.7)
+    big = _block_diag_with_identity(A, 70000 - A.n)
+    As, Ab = dev_csr(p, torch, A, dtype=tdt), dev_csr(p, torch, big, dtype=tdt)
+    rng = np.random.default_rng(side)
+    v = rng.standard_normal(A.n)
+    vb = np.concatenate([v, rng.standard_normal(big.n - A.n)])
+    for roots in (ROOTS, ROOTS[:6], np.array([3.0 + 0j]), np.array([3 + 1j, 3 - 1j])):
+        R = p.Roots.from_complex(roots)
+        ys = p.apply_poly(As, R, to_dev(torch, v, tdt))
+        yb = p.apply_poly(Ab, R, to_dev(torch, vb, tdt))
+        assert torch.equal(ys, yb[: A.n]), roots
+        fs = p.apply_phi(As, R, to_dev(torch, v, tdt))
+        fb = p.apply_phi(Ab, R, to_dev(torch, vb, tdt))
+        assert torch.equal(fs, fb[: A.n]), roots
