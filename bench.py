@@ -382,6 +382,15 @@ def run_ours(args, rank, local, world):
     poly_launches = sum(s["poly_launches"] for s in stats)
     achieved = poly_bytes / (poly_ms * 1e-3) / 1e9 if poly_ms > 0 else None
     peak, peak_kind = _peaks()
+    # the FP64 pipe beside HBM: at this size the matrix stays in L2 and the
+    # root steps are bound by FP64 issue (two FMAs per clock per SM on
+    # GB300); one FMA per nonzero plus, on average over a chain's
+    # alternating pair steps, one per row in the epilogues
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    clk_mhz = clk.get("sm_mhz") or 2070.0
+    fma_per_launch = P.A.nnz + P.A.n
+    fp64_peak = 2.0 * sms * clk_mhz * 1e-3   # G FMA / s at the sampled SM clock
+    fp64_achieved = poly_launches * fma_per_launch / (poly_ms * 1e-3) / 1e9 if poly_ms > 0 else None
     traffic = _ncu_traffic()
     ratio_c2 = _inchain_ratio("inchain_spmv_root_cd2d_1000.md", "dram_to_algorithmic_phi_f64")
 
@@ -443,7 +452,13 @@ def run_ours(args, rank, local, world):
                      "dram_note": "in-chain ncu DRAM bytes / algorithmic bytes = %s here: the "
                                   "matrix and vectors stay in L2 across the roots" % ratio_c2,
                      "traffic": traffic, "launches": poly_launches,
-                     "bytes_per_launch": round(poly_bytes / max(poly_launches, 1))},
+                     "bytes_per_launch": round(poly_bytes / max(poly_launches, 1)),
+                     "fp64": {"fma_per_launch": fma_per_launch,
+                              "achieved_gfma_s": round(fp64_achieved, 1) if fp64_achieved else None,
+                              "peak_gfma_s": round(fp64_peak, 1),
+                              "frac": round(fp64_achieved / fp64_peak, 4) if fp64_achieved else None,
+                              "peak_note": "2 FP64 FMA per clock per SM (ncu dfma peak) x %d SMs x "
+                                           "the median SM clock sampled in the timed region" % sms}},
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
