@@ -360,12 +360,15 @@ k_spmv_step(const StepArgs<T> a) {
 // chain of a step is row pointers -> (wait) -> gathers -> epilogue.  Each
 // row is summed in stored order with one FMA per nonzero and the same
 // epilogue as k_spmv_step: bit-identical results.  Two uses:
-// * small systems (PRE = 8, no register bound): a step is a handful of CTAs,
-//   and latency, not bytes, sets its time;
+// * small systems (PRE = 8, no register bound, CTAs of DIRECT_SMALL_ROWS
+//   rows): a step is a handful of CTAs, and latency, not bytes, sets its
+//   time;
 // * a matrix held in L2 (F_KEEP_A; PRE = 3 or 4 and 32 registers, 8 CTAs
 //   per SM; the preloads carry the evict-last hint): the staging round trip
 //   is then the longer path.  2-D 1000^2 FP64 chains 57.3 -> 55.2 ms.
 // MINB: minimum CTAs per SM given to __launch_bounds__ (0: no register bound).
+// One row per thread of any CTA size up to SPMV_ROWS; the residual's partial
+// sums are one per CTA.
 template <typename T>
 __device__ __forceinline__ T ld_hint(const T* p, uint64_t pol);
 template <>
@@ -387,12 +390,14 @@ __device__ __forceinline__ int32_t ld_hint<int32_t>(const int32_t* p, uint64_t p
     return v;
 }
 
+constexpr int DIRECT_SMALL_ROWS = 64;   // rows (threads) per CTA for small systems
+
 template <typename T, int OP, int PRE, int MINB, bool HINT>
 __global__ void __launch_bounds__(SPMV_ROWS, MINB)
 k_spmv_direct(const StepArgs<T> a) {
     __shared__ double sred[SPMV_ROWS / 32];
     const int tid = threadIdx.x;
-    const int64_t r = (int64_t)blockIdx.x * SPMV_ROWS + tid;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + tid;
     const bool live = r < a.n;
     asm volatile("griddepcontrol.launch_dependents;");
     int32_t k0 = 0, k1 = 0;
@@ -441,7 +446,7 @@ k_spmv_direct(const StepArgs<T> a) {
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < SPMV_ROWS / 32; ++w) t += sred[w];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sred[w];
             a.part[blockIdx.x] = t;
         }
     }
@@ -699,9 +704,18 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
         // the pair step 55.2 ms; three everywhere 55.7; five at 40 registers
         // 55.4)
         cudaError_t ed;
-        if (small)
+        if (small) {
+            // 64-row CTAs (the residual keeps 256: one partial sum per 256
+            // rows): a small system's step then spreads over 4x the SMs
+            // (2-D 50^2 p(A) v 37.9 -> 32.7 us; 128 rows 35.6, 32 rows 36.8;
+            // 100^2 56.1 -> 49.5 us)
+            if (op != OP_RESID) {
+                cfg.blockDim = dim3(DIRECT_SMALL_ROWS);
+                cfg.gridDim = dim3((unsigned)(((int64_t)a_in.n + DIRECT_SMALL_ROWS - 1) /
+                                              DIRECT_SMALL_ROWS));
+            }
             ed = launch_direct<T, 8, 0, false>(cfg, op, a);
-        else if (op == OP_PHI_PAIR2)
+        } else if (op == OP_PHI_PAIR2)
             ed = launch_direct<T, 3, 8, true>(cfg, op, a);
         else
             ed = launch_direct<T, 4, 8, true>(cfg, op, a);
