@@ -10,6 +10,9 @@ benchmark times (run with -m gpu).
   the oracle's (degree 60), FP32 p(A) v on three seeded vectors against the
   oracle's float32 Algorithm 3 (as accurate as it, both against FP64), and
   the FP32-inner flexible solve checked by its true residual.
+* 3-D convection-diffusion 100^3 (n = 1e6): in FP64 a matrix whose chains
+  hold their leading rows in L2 and stream the rest, in FP32 one held in L2
+  entirely: p(A) v and phi(A) v against the oracle.
 """
 import numpy as np
 import pytest
@@ -169,3 +172,47 @@ def test_cd3d_160_flex_solve(env, cd3d):
     x, st = p.solve_flex(A64, A32, to_dev(torch, P.b), R, P.m, P.tol)
     rel = np.linalg.norm(P.b - P.A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(P.b)
     assert st["converged"] == 1 and rel <= P.tol
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_cd3d_100_apply_with_leading_rows_held_in_l2(env, dtype):
+    """3-D convection-diffusion 100^3 (n = 1e6, 7e6 nonzeros).  In FP64 the
+    matrix and three vectors are too large for L2, so a chain streams the
+    matrix and holds the nonzeros of its leading rows (about half of them)
+    in an L2 set-aside; in FP32 they fit, and the whole matrix is held in L2
+    (the direct-read step).  p(A) v and phi(A) v against the oracle element
+    by element: FP64 within 1e-11 ||p(A)||_2 ||v||; FP32 as accurate as the
+    oracle's float32 Algorithm 3 (error against FP64 at most 3x the
+    oracle's)."""
+    p, torch = env
+    from gpu_util import p_norm_estimate
+    A = synth.cd3d(100, (0.8, 0.4, 0.2))
+    As = A.to_scipy()
+    roots = np.array([4.0, 3 + 1j, 3 - 1j, 2.5, 2 + 0.5j, 2 - 0.5j, 3.3], dtype=complex)
+    R = p.Roots.from_complex(roots)
+    v = np.random.default_rng(17).standard_normal(A.n)
+    if dtype == "f64":
+        Ad = dev_csr(p, torch, A)
+        yp = p.apply_poly(Ad, R, to_dev(torch, v)).cpu().numpy()
+        yf = p.apply_phi(Ad, R, to_dev(torch, v)).cpu().numpy()
+        rp = poly.apply_p(As, roots, v)
+        rf = poly.apply_phi(As, roots, v)
+        ATs = As.T.tocsr()
+        pn = p_norm_estimate(lambda u: poly.apply_p(As, roots, u),
+                             lambda u: poly.apply_p(ATs, roots, u), A.n, iters=15)
+        phin = p_norm_estimate(lambda u: poly.apply_phi(As, roots, u),
+                               lambda u: poly.apply_phi(ATs, roots, u), A.n, iters=15)
+        nv = np.linalg.norm(v)
+        assert np.max(np.abs(yp - rp)) <= 1e-11 * pn * nv
+        assert np.linalg.norm(yp - rp) <= 1e-11 * pn * nv
+        assert np.max(np.abs(yf - rf)) <= 1e-11 * phin * nv
+        assert np.linalg.norm(yf - rf) <= 1e-11 * phin * nv
+    else:
+        Ad = dev_csr(p, torch, A, dtype=torch.float32)
+        v32 = v.astype(np.float32)
+        y = p.apply_poly(Ad, R, to_dev(torch, v32, torch.float32)).cpu().numpy().astype(np.float64)
+        r32 = gmres.apply_p32(As.astype(np.float32), gmres._roots32(roots), v32).astype(np.float64)
+        r64 = poly.apply_p(As, roots, v32.astype(np.float64))
+        e_orc = np.linalg.norm(r32 - r64)
+        assert np.linalg.norm(y - r64) <= 3.0 * e_orc
+        assert np.linalg.norm(y - r32) <= 4.0 * e_orc
