@@ -518,23 +518,27 @@ __global__ void k_bgivens(BState st, int nsolve, int ldh, int m, int j, const do
     if (sv < nsolve) bgivens_one(sv, st, nsolve, ldh, m, j, h1, h2, nrm, build, tol);
 }
 
-// w[r, k] *= scale[solve(r, k)] for elements e = e0, e0 + stride, ...
+// w[r, k] *= scale[solve(r, k)] for elements e = e0, e0 + stride, ...; with
+// w32, also its FP32 copy, which the next Arnoldi step's Algorithm 3 chain
+// reads (the scaling of a basis column and that cast in one pass)
 template <int NR>
 __device__ __forceinline__ void bscale_range(double* w, const double* scale,
                                              const int32_t* sys_of_tile, int64_t total,
-                                             int64_t e0, int64_t stride) {
+                                             int64_t e0, int64_t stride, float* w32) {
     for (int64_t e = e0; e < total; e += stride) {
         const int64_t row = e / NR;
         const int sv = sys_of_tile[row / BT] * NR + (int)(e % NR);
-        w[e] *= scale[sv];
+        const double t = w[e] * scale[sv];
+        w[e] = t;
+        if (w32) w32[e] = (float)t;
     }
 }
 
 template <int NR>
 __global__ void k_bscale(double* w, const double* scale, const int32_t* sys_of_tile,
-                         int64_t total) {
+                         int64_t total, float* w32) {
     bscale_range<NR>(w, scale, sys_of_tile, total, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                     (int64_t)gridDim.x * blockDim.x);
+                     (int64_t)gridDim.x * blockDim.x, w32);
 }
 
 // one warp per solve: row i from the bottom up, the lanes sharing the sum
@@ -649,11 +653,6 @@ __global__ void k_unpack_vec(const double* src, int32_t n, int NR, int64_t row_o
     }
 }
 
-__global__ void k_cast64(const double* x, float* y, int64_t n) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x)
-        y[e] = (float)x[e];
-}
 __global__ void k_cast32(const float* x, double* y, int64_t n) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -813,12 +812,10 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
         if (!any_active(a.st.active, nsolve)) break;
         ++cycles;
         for (int j = 0; j < a.m; ++j) {
-            double* vj = a.V + (size_t)j * ldV;
             double* w = a.V + (size_t)(j + 1) * ldV;
             float* zj = a.Z + (size_t)j * ldV;
-            for (int64_t e = gtid; e < total; e += gstride) a.x32[e] = (float)vj[e];
-            PSYNC();
-            // z_j = p(A) v_j: Algorithm 3 in FP32, one pass per step
+            // z_j = p(A) v_j: Algorithm 3 in FP32, one pass per step (its FP32
+            // copy x32 of v_j was written with the scaling of v_j)
             BufSet<float> fs{};
             fs.p[B_IN] = a.x32;
             fs.p[B_P] = zj;
@@ -879,7 +876,7 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
             for (int64_t sv = gtid; sv < nsolve; sv += gstride)
                 bgivens_one((int)sv, a.st, nsolve, a.ldh, a.m, j, a.h1, a.h2, a.nrm, 0, a.tol);
             PSYNC();
-            bscale_range<NR>(w, a.st.inv, a.sys_of_tile, total, gtid, gstride);
+            bscale_range<NR>(w, a.st.inv, a.sys_of_tile, total, gtid, gstride, a.x32);
             PSYNC();
             if (!any_active(a.st.active, nsolve)) break;
         }
@@ -906,7 +903,7 @@ __global__ void __launch_bounds__(256, 4) k_bpersist(const PArgs a) {
         for (int64_t sv = gtid; sv < nsolve; sv += gstride)
             bcycle_one((int)sv, a.st, a.m, a.nrm, a.tol, 0);
         PSYNC();
-        bscale_range<NR>(a.V, a.st.inv, a.sys_of_tile, total, gtid, gstride);
+        bscale_range<NR>(a.V, a.st.inv, a.sys_of_tile, total, gtid, gstride, a.x32);
         PSYNC();
     }
     if (blockIdx.x == 0 && tid == 0) *a.cycles_out = cycles;
@@ -1069,11 +1066,9 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
     const int64_t total = B.N * NR;
     const int sg = (nsolve + 127) / 128;
     for (int j = 0; j < B.m; ++j) {
-        double* vj = W.V + (size_t)j * ldV;
         double* w = W.V + (size_t)(j + 1) * ldV;
         float* zj = W.Z + (size_t)j * ldV;
-        k_cast64<<<elem_grid(total), 256, 0, s>>>(vj, W.v32, total);
-        BCHECK("k_cast64");
+        // (W.v32 = v_j in FP32 was written with the scaling of v_j)
         BufSet<float> fs{};
         fs.p[B_IN] = W.v32;
         fs.p[B_P] = zj;
@@ -1092,7 +1087,7 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
         PPG_TRY(cgs2_batch<NR>(B, W, j, w, 0, ldV, s, W.st.active));
         k_bgivens<<<sg, 128, 0, s>>>(W.st, nsolve, B.ldh, B.m, j, W.h1, W.h2, W.nrm, 0, tol);
         BCHECK("k_bgivens");
-        k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(w, W.st.inv, B.sys_of_tile, total);
+        k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(w, W.st.inv, B.sys_of_tile, total, W.v32);
         BCHECK("k_bscale");
     }
     k_bbacksolve<<<(unsigned)(((int64_t)nsolve * 32 + 127) / 128), 128, 0, s>>>(W.st, nsolve, B.ldh,
@@ -1109,7 +1104,7 @@ int32_t cycle_batch(Batch& B, Work& W, int K, double tol, cudaStream_t s) {
     BCHECK("k_bsegsum");
     k_bcycle<<<sg, 128, 0, s>>>(W.st, nsolve, B.m, W.nrm, tol, 0);
     BCHECK("k_bcycle");
-    k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(W.V, W.st.inv, B.sys_of_tile, total);
+    k_bscale<NR><<<elem_grid(total), 256, 0, s>>>(W.V, W.st.inv, B.sys_of_tile, total, W.v32);
     BCHECK("k_bscale");
     return PPG_OK;
 }
@@ -1382,7 +1377,7 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
         PPG_CUDA(cudaMemsetAsync(bst.brk, 0xff, sizeof(int32_t) * nsys, s));
         k_bcycle<<<sg1, 128, 0, s>>>(bst, nsys, mk, W.nrm, -1.0, 1);   // inv = 1/||v0||
         BCHECK("k_bcycle");
-        k_bscale<1><<<elem_grid(N), 256, 0, s>>>(W.V, bst.inv, B.sys_of_tile, N);
+        k_bscale<1><<<elem_grid(N), 256, 0, s>>>(W.V, bst.inv, B.sys_of_tile, N, nullptr);
         BCHECK("k_bscale");
         std::vector<BStep> hs(nsys);
         for (auto& st : hs) st = BStep{OP_SPMV, 0, 0, 0, 0, B_IN, -1, -1, -1, B_OUT, -1};
@@ -1398,7 +1393,7 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
             PPG_TRY(cgs2_batch<1>(B, W, j, w, 1, N, s));
             k_bgivens<<<sg1, 128, 0, s>>>(bst, nsys, B.ldh, mk, j, W.h1, W.h2, W.nrm, 1, 0.0);
             BCHECK("k_bgivens");
-            k_bscale<1><<<elem_grid(N), 256, 0, s>>>(w, bst.inv, B.sys_of_tile, N);
+            k_bscale<1><<<elem_grid(N), 256, 0, s>>>(w, bst.inv, B.sys_of_tile, N, nullptr);
             BCHECK("k_bscale");
         }
         std::vector<double> H((size_t)nsys * B.ldh * mk);
@@ -1484,7 +1479,7 @@ static int32_t solve_batched_impl(int32_t nsys, const ppg_csr* As, const double*
     BCHECK("k_bsegsum");
     k_bcycle<<<sgn, 128, 0, s>>>(W.st, nsolve, m, W.nrm, tol, 1);
     BCHECK("k_bcycle");
-    k_bscale<NR><<<elem_grid(ldV), 256, 0, s>>>(W.V, W.st.inv, B.sys_of_tile, ldV);
+    k_bscale<NR><<<elem_grid(ldV), 256, 0, s>>>(W.V, W.st.inv, B.sys_of_tile, ldV, W.v32);
     BCHECK("k_bscale");
     // the Krylov state of the solve uses m columns
     Batch Bs = B;
