@@ -1,29 +1,37 @@
 // Fused CSR SpMV + root update: one pass over A per root of the GMRES
 // polynomial (Algorithm 1: phi(A) v, Algorithm 3: p(A) v), plus the plain
-// SpMV and the residual b - A x.
+// SpMV and the residual b - A x.  Two kernels with the same arithmetic
+// (each row summed in stored order, one fused multiply-add per nonzero,
+// acc = fma(val, x[col], acc), then the same epilogue), so their results
+// are bit-identical:
 //
-// Layout: a CTA owns a tile of SPMV_ROWS consecutive rows.  It copies the
-// tile's column indices and values into shared memory with asynchronous,
-// fully coalesced copies (cp.async; consecutive threads take consecutive
-// nonzeros, so short rows of 5-7 entries leave no lane idle), then thread t
-// walks row t of the tile with one fused multiply-add per nonzero,
-// acc = fma(val, x[col], acc), and applies the root update in the epilogue,
-// reading and writing the row-aligned vectors once, coalesced.  Tiles whose
-// nonzeros exceed the staging buffer are processed in chunks, so any row
-// length is handled.
+// k_spmv_step, for a matrix streamed from HBM: a CTA owns a tile of rows
+// (256 in FP64, 512 in FP32: two per thread).  It copies the tile's column
+// indices and values into shared memory with asynchronous, coalesced
+// 16-byte copies (consecutive threads take consecutive granules, so short
+// rows of 5-7 entries leave no lane idle), then each thread walks its rows
+// and applies the root update in the epilogue, reading and writing the
+// row-aligned vectors once, coalesced.  Tiles whose nonzeros exceed the
+// staging buffer are processed in chunks, so any row length is handled.
+//
+// k_spmv_direct, for small systems and for a matrix held in L2: one row per
+// thread, its first entries read straight into registers before the wait on
+// the previous step (no staging round trip).
 //
 // GB300 executes about two FP64 operations per clock per SM, so in FP64 the
-// multiply-adds, not only the bytes, bound this kernel: one FMA per nonzero
-// is the minimum and the epilogues use fused forms.
+// multiply-adds, not only the bytes, bound these kernels: one FMA per
+// nonzero is the minimum and the epilogues use fused forms.
 //
 // Consecutive steps overlap: each is launched as a programmatic dependent of
-// the previous one and stages its share of the matrix before it waits for
-// the previous step's vectors.
+// the previous one and reads its share of the matrix before it waits for the
+// previous step's vectors.
 //
 // L2 policy: when the matrix and the chain's vectors fit in L2, the matrix is
-// copied with an evict-last hint and stays resident across the roots of a
-// chain (every root reads the same A); otherwise with evict-first, so that
-// streaming A does not push the vectors out.
+// read with an evict-last hint into a set-aside and stays resident across
+// the roots of a chain (every root reads the same A).  Otherwise a chain
+// holds the nonzeros of its leading rows that way in a 48 MB set-aside and
+// streams the rest with evict-first, prefetching it into L2 half a resident
+// wave ahead.
 #include <atomic>
 
 #include "ppg_common.cuh"
