@@ -18,16 +18,21 @@
 // step it applies is uniform over the CTA.
 //
 // Krylov part.  CGS2 runs as in the single-system solver, with the dot
-// products reduced per tile and then per system in a fixed order
-// (deterministic); one thread per solve applies the Givens rotations and
-// decides on the device whether its solve stops in this cycle, so a whole
-// restart cycle needs no host synchronisation and is captured once as a
-// CUDA graph and replayed for every cycle.  CTAs of a system whose solves
-// have all stopped return at once, so converged systems cost next to
-// nothing in later steps and cycles.
+// products reduced per unit of up to 8 tiles and then per system in a fixed
+// order (deterministic); one thread per solve applies the Givens rotations
+// and decides on the device whether its solve stops in this cycle, so no
+// step needs the host.  CTAs of a system whose solves have all stopped
+// return at once, so converged systems cost next to nothing in later steps
+// and cycles.
 //
-// Tiling.  The rows per CTA of the FP32 root-step kernel (64, 128 or 256)
-// are chosen by timing the candidates on the batch at set-up.
+// Launch shape.  By default the whole solve, every restart cycle, runs in
+// one persistent cooperative kernel (k_bpersist, its phases separated by
+// bounded grid barriers); alternatively one restart cycle is captured once
+// as a CUDA graph of the per-phase kernels and replayed for every cycle.
+//
+// Tiling.  The rows per CTA of the graph form's FP32 root-step kernel (64,
+// 128 or 256) are chosen by timing the candidates on the batch at set-up;
+// the persistent kernel runs its root steps on row groups of 64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
