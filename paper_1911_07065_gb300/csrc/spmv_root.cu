@@ -399,6 +399,7 @@ __device__ __forceinline__ int32_t ld_hint<int32_t>(const int32_t* p, uint64_t p
 }
 
 constexpr int DIRECT_SMALL_ROWS = 64;   // rows (threads) per CTA for small systems
+constexpr int DIRECT_L2_ROWS = 128;     // ... and for a matrix held in L2
 
 template <typename T, int OP, int PRE, int MINB, bool HINT>
 __global__ void __launch_bounds__(SPMV_ROWS, MINB)
@@ -723,10 +724,19 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
                                               DIRECT_SMALL_ROWS));
             }
             ed = launch_direct<T, 8, 0, false>(cfg, op, a);
-        } else if (op == OP_PHI_PAIR2)
-            ed = launch_direct<T, 3, 8, true>(cfg, op, a);
-        else
-            ed = launch_direct<T, 4, 8, true>(cfg, op, a);
+        } else {
+            // matrix in L2: 128-row CTAs (2-D 1000^2 FP64 chains 55.22 ->
+            // 54.88 ms against 256 rows; 64 rows 69.5 ms)
+            if (op != OP_RESID) {
+                cfg.blockDim = dim3(DIRECT_L2_ROWS);
+                cfg.gridDim = dim3((unsigned)(((int64_t)a_in.n + DIRECT_L2_ROWS - 1) /
+                                              DIRECT_L2_ROWS));
+            }
+            if (op == OP_PHI_PAIR2)
+                ed = launch_direct<T, 3, 8, true>(cfg, op, a);
+            else
+                ed = launch_direct<T, 4, 8, true>(cfg, op, a);
+        }
         ++g_launches;
         if (ed != cudaSuccess) {
             set_cuda_error(ed, "cudaLaunchKernelEx(k_spmv_direct)");
