@@ -158,6 +158,10 @@ __device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T
 template <typename T>
 __host__ __device__ constexpr int step_rpt() { return sizeof(T) == 4 ? 2 : 1; }
 
+// Threads per CTA of the staged step
+template <typename T>
+__host__ __device__ constexpr int step_threads() { return 256; }
+
 // Nonzeros staged per chunk: FP64 2048 (256 rows of up to 8); FP32 3584, so
 // that a tile of 512 rows of a 7-point stencil is one chunk and the CTA's
 // 30.7 KB of shared memory lets 7 CTAs share an SM (with 4096, 6 fit:
@@ -214,17 +218,18 @@ __device__ __forceinline__ T row_dot(const T* sval, const int32_t* scol, const T
 // PF: prefetch the tile a.pf_ahead tiles ahead (half a resident wave) into
 // L2 (launched when the matrix is not held in an L2 set-aside)
 template <typename T, int OP, bool PF>
-__global__ void __launch_bounds__(SPMV_ROWS, step_min_ctas<T, OP>())
+__global__ void __launch_bounds__(step_threads<T>(), step_min_ctas<T, OP>())
 k_spmv_step(const StepArgs<T> a) {
+    constexpr int NT = step_threads<T>();      // threads per CTA
     // staging copies start at a chunk base rounded down to 4 elements
     constexpr int PAD = 4;
     constexpr int RPT = step_rpt<T>();
-    constexpr int ROWS = SPMV_ROWS * RPT;      // rows per CTA
+    constexpr int ROWS = NT * RPT;      // rows per CTA
     constexpr int CHUNK = step_chunk<T>();     // nonzeros staged per chunk
     __shared__ __align__(16) T sval[CHUNK + PAD];
     __shared__ __align__(16) int32_t scol[CHUNK + PAD];
     __shared__ int32_t srp[ROWS + 1];
-    __shared__ double sred[SPMV_ROWS / 32];
+    __shared__ double sred[NT / 32];
 
     const int64_t row0 = (int64_t)blockIdx.x * ROWS;
     const int tid = threadIdx.x;
@@ -251,15 +256,15 @@ k_spmv_step(const StepArgs<T> a) {
         pk0 = __ldg(a.rowptr + prow);
         pk1 = __ldg(a.rowptr + prow1);
     }
-    for (int i = tid; i <= nrows; i += SPMV_ROWS) srp[i] = __ldg(a.rowptr + row0 + i);
+    for (int i = tid; i <= nrows; i += NT) srp[i] = __ldg(a.rowptr + row0 + i);
     __syncthreads();
     const int32_t k0 = srp[0];
     const int32_t k1 = srp[nrows];
-    // thread tid owns rows tid and (RPT = 2) tid + SPMV_ROWS of the tile
+    // thread tid owns rows tid and (RPT = 2) tid + NT of the tile
     int32_t my_lo[RPT], my_hi[RPT];
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SPMV_ROWS;
+        const int t = tid + q * NT;
         my_lo[q] = (t < nrows) ? srp[t] : k1;
         my_hi[q] = (t < nrows) ? srp[t + 1] : k1;
     }
@@ -268,7 +273,7 @@ k_spmv_step(const StepArgs<T> a) {
     {
         const int32_t c1 = min(k1, k0 + CHUNK);
         const int32_t base = k0 & ~3;
-        stage_chunk<T>(sval, scol, a.vals, a.colind, base, k0, c1, tid, SPMV_ROWS,
+        stage_chunk<T>(sval, scol, a.vals, a.colind, base, k0, c1, tid, NT,
                        l2_policy(keep));
     }
     if (pf) {
@@ -295,7 +300,7 @@ k_spmv_step(const StepArgs<T> a) {
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
         e0[q] = e1[q] = e2[q] = acc[q] = T(0);
-        const int t = tid + q * SPMV_ROWS;
+        const int t = tid + q * NT;
         if (t < nrows) {
             const int64_t rr = row0 + t;
             if (a.a0) e0[q] = __ldg(a.a0 + rr);
@@ -308,7 +313,7 @@ k_spmv_step(const StepArgs<T> a) {
         const int32_t c1 = min(k1, c0 + CHUNK);
         const int32_t base = c0 & ~3;
         if (c0 != k0) {   // the first chunk was issued before the wait
-            stage_chunk<T>(sval, scol, a.vals, a.colind, base, c0, c1, tid, SPMV_ROWS,
+            stage_chunk<T>(sval, scol, a.vals, a.colind, base, c0, c1, tid, NT,
                            l2_policy(keep));
         }
         cp_async_wait_all();
@@ -346,7 +351,7 @@ k_spmv_step(const StepArgs<T> a) {
     double sq = 0.0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SPMV_ROWS;
+        const int t = tid + q * NT;
         if (t < nrows) step_epilogue<T, OP>(a, row0 + t, acc[q], e0[q], e1[q], e2[q], sq);
     }
     if constexpr (OP == OP_RESID) {
@@ -356,7 +361,7 @@ k_spmv_step(const StepArgs<T> a) {
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
-            for (int w = 0; w < SPMV_ROWS / 32; ++w) t += sred[w];
+            for (int w = 0; w < NT / 32; ++w) t += sred[w];
             a.part[blockIdx.x] = t;
         }
     }
@@ -632,7 +637,7 @@ static int step_resident_ctas() {
     if (v == 0) {
         int occ = 0, sms = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_step<T, OP_P_REAL, true>,
-                                                          SPMV_ROWS, 0) != cudaSuccess ||
+                                                          step_threads<T>(), 0) != cudaSuccess ||
             occ < 1)
             occ = 1;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -681,7 +686,7 @@ static cudaError_t launch_op(cudaLaunchConfig_t& cfg, int op, const StepArgs<T>&
 template <typename T>
 int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     if (a_in.n <= 0) return 0;
-    const int rows = SPMV_ROWS * step_rpt<T>();
+    const int rows = step_threads<T>() * step_rpt<T>();
     const int grid = (int)(((int64_t)a_in.n + rows - 1) / rows);
     StepArgs<T> a = a_in;
     // prefetch half a resident wave ahead, unless the matrix is held in an
@@ -692,7 +697,7 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
     a.pf_ahead = (a.flags & F_KEEP_A) ? 0 : (step_resident_ctas<T>() + 1) / 2;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(SPMV_ROWS);
+    cfg.blockDim = dim3(step_threads<T>());
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -706,6 +711,7 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
         // one row per thread, no staging round (small system, or matrix in L2)
         const int dgrid = (int)(((int64_t)a_in.n + SPMV_ROWS - 1) / SPMV_ROWS);
         cfg.gridDim = dim3(dgrid);
+        cfg.blockDim = dim3(SPMV_ROWS);
         // matrix in L2: four entries preloaded at 32 registers (8 CTAs per SM),
         // three for the second step of a pair of Algorithm 1, which spills at
         // four (2-D 1000^2 FP64 chains: staged kernel 57.3 ms; direct with
