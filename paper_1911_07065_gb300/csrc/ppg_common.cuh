@@ -178,6 +178,7 @@ int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_
 int keep_a_flag(int64_t n, int64_t nnz, int elem, int nvec, bool may_reserve = true,
                 int32_t* keep_rows = nullptr);
 
+// at least the partial sums any residual step of n rows writes (one per CTA)
 int32_t spmv_grid_blocks(int32_t n);
 
 // algorithmic bytes of one fused step

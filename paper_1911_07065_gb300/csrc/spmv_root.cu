@@ -154,28 +154,30 @@ __device__ __forceinline__ void step_epilogue(const StepArgs<T>& a, int64_t r, T
 
 // Rows per thread: FP32 tiles take two rows per thread (512 rows per CTA),
 // so each CTA's latency-bound phases (row pointers, staging, gathers) serve
-// twice the bytes; FP64 keeps one (its 32 registers allow 8 CTAs per SM).
+// twice the bytes; FP64 keeps one (at 32 registers, 2048 threads per SM).
 template <typename T>
 __host__ __device__ constexpr int step_rpt() { return sizeof(T) == 4 ? 2 : 1; }
 
-// Threads per CTA of the staged step
+// Threads per CTA of the staged step: FP64 128 (tiles of 128 rows, 16 CTAs
+// per SM; 3-D 160^3 FP64 chains 6220 -> 6390 GB/s against 256, 6070 with
+// 64), FP32 256 (tiles of 512 rows; 128 threads measured the same)
 template <typename T>
-__host__ __device__ constexpr int step_threads() { return 256; }
+__host__ __device__ constexpr int step_threads() { return sizeof(T) == 4 ? 256 : 128; }
 
-// Nonzeros staged per chunk: FP64 2048 (256 rows of up to 8); FP32 3584, so
+// Nonzeros staged per chunk: FP64 1024 (128 rows of up to 8); FP32 3584, so
 // that a tile of 512 rows of a 7-point stencil is one chunk and the CTA's
 // 30.7 KB of shared memory lets 7 CTAs share an SM (with 4096, 6 fit:
 // 3-D 160^3 FP32 chains 1 % slower).  Longer tiles take several chunks.
 template <typename T>
-__host__ __device__ constexpr int step_chunk() { return sizeof(T) == 4 ? 3584 : 2048; }
+__host__ __device__ constexpr int step_chunk() { return sizeof(T) == 4 ? 3584 : 1024; }
 
 // CTAs per SM the register budget must allow (FP32: 32 registers instead
-// of 40; FP64 already compiles to 32).  The FP32 second step of a pair of
+// of 40; FP64: 16 CTAs of 128 threads, 32 registers).  The FP32 second step of a pair of
 // Algorithm 1 (not on the precision form's path, which applies p(A) only)
 // keeps 40 registers and 6 CTAs: at 32 it spills.
 template <typename T, int OP>
 __host__ __device__ constexpr int step_min_ctas() {
-    return sizeof(T) == 4 ? (OP == OP_PHI_PAIR2 ? 6 : 7) : 8;
+    return sizeof(T) == 4 ? (OP == OP_PHI_PAIR2 ? 6 : 7) : 16;
 }
 
 // one row's multiply-adds over its staged nonzeros [lo, hi): four gathers in
@@ -516,7 +518,15 @@ int32_t launch_ew_step(int op, const StepArgs<T>& a, const T* prodv, cudaStream_
 template int32_t launch_ew_step<double>(int, const StepArgs<double>&, const double*,
                                         cudaStream_t);
 
-int32_t spmv_grid_blocks(int32_t n) { return (n + SPMV_ROWS - 1) / SPMV_ROWS; }
+// An upper bound on the partial sums a residual step of n rows writes (one
+// per CTA): the smallest tile of any kernel that computes one (the staged
+// FP64 step's 128 rows; the direct step's residual keeps 256-row CTAs)
+int32_t spmv_grid_blocks(int32_t n) {
+    constexpr int r64 = step_threads<double>() * step_rpt<double>();
+    constexpr int r32 = step_threads<float>() * step_rpt<float>();
+    constexpr int rmin = r64 < r32 ? (r64 < SPMV_ROWS ? r64 : SPMV_ROWS) : (r32 < SPMV_ROWS ? r32 : SPMV_ROWS);
+    return (int32_t)(((int64_t)n + rmin - 1) / rmin);
+}
 
 // Reserve L2 for evict-last (persisting) lines on the current device: without
 // a set-aside the evict-last hint is treated as normal.  This is a limit of
