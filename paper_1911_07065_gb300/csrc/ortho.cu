@@ -24,15 +24,24 @@ constexpr int ORTHO_THREADS = 256;
 constexpr int ORTHO_WARPS = ORTHO_THREADS / 32;
 constexpr int DOT_CH = 8;                 // columns per register chunk
 constexpr int PART_STRIDE = ORTHO_MAXC + 2;
+// threads per CTA of the two streaming CGS2 passes (k_mdot, k_gemv_sub),
+// their minimum CTAs per SM, and the most row blocks they launch (one wave)
+constexpr int CGS_THREADS = 256;
+constexpr int CGS_WARPS = CGS_THREADS / 32;
+constexpr int CGS_DOT_MINB = 4 * 256 / CGS_THREADS;
+constexpr int CGS_SUB_MINB = 5 * 256 / CGS_THREADS;
+inline int cgs_max_blocks() { return grid_cap(8 * 256 / CGS_THREADS); }
 
 int ortho_grid(int32_t n) {
     const int per = ORTHO_THREADS * 8;   // at least ~8 rows per thread
     return max(1, min((n + per - 1) / per, grid_cap(2)));
 }
 
-// partial sums of the CGS2 passes: their grids have at most grid_cap(8) row
-// blocks (the norm kernels at most `grid`)
-size_t ortho_part_doubles(int grid) { return (size_t)max(grid, grid_cap(8)) * PART_STRIDE; }
+// partial sums of the CGS2 passes: their grids have at most cgs_max_blocks()
+// row blocks (the norm kernels at most `grid`)
+size_t ortho_part_doubles(int grid) {
+    return (size_t)max(grid, max(grid_cap(8), cgs_max_blocks())) * PART_STRIDE;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -70,7 +79,7 @@ __device__ __forceinline__ void warp_reduce8(double v[8], int lane) {
 // order, into out[c].  Called by every thread of the last CTA.
 __device__ void final_reduce(const double* part, int nblocks, int nvals, double* out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int c = warp; c < nvals; c += ORTHO_WARPS) {
+    for (int c = warp; c < nvals; c += (int)(blockDim.x >> 5)) {
         double s = 0.0;
         for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * PART_STRIDE + c);
         s = warp_sum(s);
@@ -136,10 +145,10 @@ __device__ __forceinline__ void dot_rows(const double* const* col, const double*
 // with_self.  Grid: x = row blocks (grid-stride), y = chunks of eight
 // columns, so every column chunk streams in parallel.
 template <bool VEC2>
-__global__ void __launch_bounds__(ORTHO_THREADS, 4)
+__global__ void __launch_bounds__(CGS_THREADS, CGS_DOT_MINB)
 k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __restrict__ w,
        int32_t n, int with_self, double* part, unsigned* counter, double* hout) {
-    __shared__ double sred[ORTHO_WARPS][DOT_CH];
+    __shared__ double sred[CGS_WARPS][DOT_CH];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nvals = ncol + (with_self ? 1 : 0);
     // gridDim.y = ceil(nvals / 8) chunks of near-equal width (at most 8), so
@@ -157,8 +166,8 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     for (int q = 0; q < DOT_CH; ++q) acc[q] = 0.0;
     PPG_PDL_TRIGGER();
     PPG_PDL_WAIT();
-    const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
-    const int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
+    const int64_t stride = (int64_t)gridDim.x * CGS_THREADS;
+    const int64_t r = (int64_t)blockIdx.x * CGS_THREADS + tid;
     switch (nq) {
         case 8: dot_rows<8, VEC2>(col, w, r, stride, n, acc); break;
         case 7: dot_rows<7, VEC2>(col, w, r, stride, n, acc); break;
@@ -175,7 +184,7 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
     if (tid < nq) {
         double t = 0.0;
 #pragma unroll
-        for (int k = 0; k < ORTHO_WARPS; ++k) t += sred[k][tid];
+        for (int k = 0; k < CGS_WARPS; ++k) t += sred[k][tid];
         part[(size_t)blockIdx.x * PART_STRIDE + c0 + tid] = t;
     }
     // the last CTA of the whole grid sums the partials of every column
@@ -193,20 +202,20 @@ k_mdot(const double* __restrict__ V, int64_t ldv, int ncol, const double* __rest
 
 // w[r] -= sum_c V[c][r] h[c]; with_norm: nout[0] = ||w||^2 afterwards
 template <bool VEC2>
-__global__ void __launch_bounds__(ORTHO_THREADS, 5)
+__global__ void __launch_bounds__(CGS_THREADS, CGS_SUB_MINB)
 k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_t n,
            const double* __restrict__ h, int with_norm, double* part, unsigned* counter,
            double* nout) {
     __shared__ double sh[ORTHO_MAXC];
-    __shared__ double sred[ORTHO_WARPS];
+    __shared__ double sred[CGS_WARPS];
     const int tid = threadIdx.x;
     PPG_PDL_TRIGGER();
     PPG_PDL_WAIT();
-    for (int c = tid; c < ncol; c += ORTHO_THREADS) sh[c] = h[c];
+    for (int c = tid; c < ncol; c += CGS_THREADS) sh[c] = h[c];
     __syncthreads();
     double nacc = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * ORTHO_THREADS;
-    int64_t r = (int64_t)blockIdx.x * ORTHO_THREADS + tid;
+    const int64_t stride = (int64_t)gridDim.x * CGS_THREADS;
+    int64_t r = (int64_t)blockIdx.x * CGS_THREADS + tid;
     if constexpr (VEC2) {
         // rows 2p and 2p+1: one 16-byte load per column, two FMA chains,
         // exactly one FMA per element of V; an odd last row goes to the one
@@ -259,7 +268,7 @@ k_gemv_sub(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32
     __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int k = 0; k < ORTHO_WARPS; ++k) t += sred[k];
+        for (int k = 0; k < CGS_WARPS; ++k) t += sred[k];
         part[(size_t)blockIdx.x * PART_STRIDE] = t;
     }
     if (last_block_done(counter)) {
@@ -529,14 +538,14 @@ k_sub_dot(const double* __restrict__ V, int64_t ldv, int ncol, double* w, int32_
 // CTAs of a kernel resident at once on the current device (occupancy x
 // SMs), cached per device and kernel slot
 template <typename K>
-static int resident_ctas(K kernel, int slot) {
+static int resident_ctas(K kernel, int slot, int threads) {
     static std::atomic<int> cached[16][4];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
     int v = cached[dev][slot].load(std::memory_order_relaxed);
     if (v == 0) {
         int occ = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, ORTHO_THREADS, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) !=
                 cudaSuccess || occ < 1)
             occ = 4;
         sms = device_sm_count();
@@ -556,17 +565,18 @@ int32_t launch_cgs_dot(const double* V, int64_t ldv, int ncol, const double* w, 
     const int nvals = ncol + (with_self ? 1 : 0);
     const int nch = (nvals + DOT_CH - 1) / DOT_CH;
     // row blocks x column chunks = one full wave of resident CTAs (at least
-    // two rows per thread; the partial-sum buffer holds grid_cap(8) row blocks)
+    // two rows per thread; the partial-sum buffer holds cgs_max_blocks() row
+    // blocks)
     const bool v2 = vec2_ok(V, ldv, w);
-    const int slots = v2 ? resident_ctas(k_mdot<true>, 0) : resident_ctas(k_mdot<false>, 1);
-    const int gx = max(1, min(min(slots / nch, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
-                              grid_cap(8)));
-    // (ws.part holds max(ws.grid, grid_cap(8)) row blocks of partial sums)
+    const int slots = v2 ? resident_ctas(k_mdot<true>, 0, CGS_THREADS)
+                         : resident_ctas(k_mdot<false>, 1, CGS_THREADS);
+    const int gx = max(1, min(min(slots / nch, (n + 2 * CGS_THREADS - 1) / (2 * CGS_THREADS)),
+                              cgs_max_blocks()));
     const dim3 grid(gx, nch);
     const cudaError_t e =
-        v2 ? launch_pdl(k_mdot<true>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
+        v2 ? launch_pdl(k_mdot<true>, grid, dim3(CGS_THREADS), 0, s, V, ldv, ncol, w, n,
                         with_self ? 1 : 0, ws.part, ws.counter, h_out)
-           : launch_pdl(k_mdot<false>, grid, dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w, n,
+           : launch_pdl(k_mdot<false>, grid, dim3(CGS_THREADS), 0, s, V, ldv, ncol, w, n,
                         with_self ? 1 : 0, ws.part, ws.counter, h_out);
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_mdot"); return PPG_ERR_CUDA; }
@@ -578,15 +588,16 @@ int32_t launch_cgs_update(const double* V, int64_t ldv, int ncol, double* w, int
                           const OrthoWs& ws, cudaStream_t s) {
     if (ncol < 1 || ncol > ORTHO_MAXC) return PPG_ERR_ARG;
     // one wave of resident CTAs, at least two rows per thread, at most the
-    // grid_cap(8) row blocks the partial-sum buffer holds
+    // cgs_max_blocks() row blocks the partial-sum buffer holds
     const bool v2 = vec2_ok(V, ldv, w);
-    const int slots = v2 ? resident_ctas(k_gemv_sub<true>, 2) : resident_ctas(k_gemv_sub<false>, 3);
-    const int grid = max(1, min(min(slots, (n + 2 * ORTHO_THREADS - 1) / (2 * ORTHO_THREADS)),
-                                grid_cap(8)));
+    const int slots = v2 ? resident_ctas(k_gemv_sub<true>, 2, CGS_THREADS)
+                         : resident_ctas(k_gemv_sub<false>, 3, CGS_THREADS);
+    const int grid = max(1, min(min(slots, (n + 2 * CGS_THREADS - 1) / (2 * CGS_THREADS)),
+                                cgs_max_blocks()));
     const cudaError_t e =
-        v2 ? launch_pdl(k_gemv_sub<true>, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv, ncol, w,
+        v2 ? launch_pdl(k_gemv_sub<true>, dim3(grid), dim3(CGS_THREADS), 0, s, V, ldv, ncol, w,
                         n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1, nrm_out)
-           : launch_pdl(k_gemv_sub<false>, dim3(grid), dim3(ORTHO_THREADS), 0, s, V, ldv, ncol,
+           : launch_pdl(k_gemv_sub<false>, dim3(grid), dim3(CGS_THREADS), 0, s, V, ldv, ncol,
                         w, n, hin, with_norm ? 1 : 0, ws.part, ws.counter + 1, nrm_out);
     ++g_launches;
     if (e != cudaSuccess) { set_cuda_error(e, "launch k_gemv_sub"); return PPG_ERR_CUDA; }
