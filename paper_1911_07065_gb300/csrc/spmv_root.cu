@@ -722,7 +722,7 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
         const int dgrid = (int)(((int64_t)a_in.n + SPMV_ROWS - 1) / SPMV_ROWS);
         cfg.gridDim = dim3(dgrid);
         cfg.blockDim = dim3(SPMV_ROWS);
-        // matrix in L2: four entries preloaded at 32 registers (8 CTAs per SM),
+        // matrix in L2: four entries preloaded at 32 registers (2048 threads per SM),
         // three for the second step of a pair of Algorithm 1, which spills at
         // four (2-D 1000^2 FP64 chains: staged kernel 57.3 ms; direct with
         // four preloads 55.8 ms (without the evict-last hint 56.3 ms); three for
