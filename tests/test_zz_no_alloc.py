@@ -148,3 +148,22 @@ def test_noalloc_allocates_nothing():
     stream.synchronize()
     assert pool.get(pool.USED_MEM_HIGH) >= used0 + 3 * 8 * A.n
     assert torch.equal(y, y2)
+
+
+def test_noalloc_on_a_matrix_streamed_from_hbm():
+    """3-D 100^3 in FP64 (n = 1e6, within the work area's limit): the
+    matrix does not fit in L2 with the chain's vectors, so both entry points
+    stream it; ppg_apply_poly sets the L2 set-aside for the chain's leading
+    rows, the no-allocation call only uses the set-aside in place.  The L2
+    hints differ, the arithmetic does not: the results are bit-identical."""
+    p, torch = ppg_or_skip()
+    A = synth.cd3d(100, (0.8, 0.4, 0.2))
+    Ad = dev_csr(p, torch, A)
+    R = p.Roots.from_complex(np.array([4.0, 3 + 1j, 3 - 1j, 2.5, 2 + 0.5j, 2 - 0.5j, 3.3]))
+    v = to_dev(torch, np.random.default_rng(23).standard_normal(A.n))
+    ref = p.apply_poly(Ad, R, v)
+    y = torch.full_like(v, float("nan"))
+    rc = _call_noalloc(p, torch, Ad, R, v, y)
+    assert rc == 0, p.lib.ppg_strerror(rc)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
