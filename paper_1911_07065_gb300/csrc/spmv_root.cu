@@ -347,7 +347,9 @@ k_spmv_step(const StepArgs<T> a) {
             acc[0] = row_dot<T, true>(sval, scol, a.x, ka, ha, acc[0]);
             acc[1] = row_dot<T, true>(sval, scol, a.x, kb, hb, acc[1]);
         }
-        __syncthreads();
+        // the staged chunk is read by every thread: a barrier before it is
+        // overwritten, none after the last one (3-D 160^3 chains +0.2 %)
+        if (c0 + CHUNK < k1) __syncthreads();
     }
 
     double sq = 0.0;
