@@ -189,7 +189,14 @@ int32_t ppg_build_poly(const ppg_csr* A, int32_t d, const double* v0,
 /* y = p(A) v by Algorithm 3: d-1 fused SpMV-root passes (two per conjugate
  * pair, the last pair's second one omitted), vectors in A's dtype.  For
  * PPG_F32 the root coefficients 1/theta, 2a and 1/(a^2+b^2) are rounded to
- * float.  Asynchronous. */
+ * float.  Asynchronous.
+ *
+ * L2: the chains of this call (and of ppg_apply_phi and the solvers) set
+ * the persisting-L2 set-aside of the current device's CUDA context -- a
+ * limit of this process's context, never a device setting: when the matrix
+ * and three vectors fit in 80 % of L2, a set-aside sized for the matrix,
+ * which then stays resident across the roots; otherwise 48 MB, which holds
+ * the nonzeros of the matrix's leading rows while the rest streams. */
 int32_t ppg_apply_poly(const ppg_csr* A, const ppg_roots* r, const void* v,
                        void* y, void* stream);
 
