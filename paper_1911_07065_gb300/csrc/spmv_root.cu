@@ -724,13 +724,15 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
         const int dgrid = (int)(((int64_t)a_in.n + SPMV_ROWS - 1) / SPMV_ROWS);
         cfg.gridDim = dim3(dgrid);
         cfg.blockDim = dim3(SPMV_ROWS);
-        // matrix in L2: four entries preloaded at 32 registers (2048 threads per SM),
-        // five for the plain SpMV step, three for the second step of a pair of
-        // Algorithm 1, which spills at four (2-D 1000^2 FP64 chains: staged
-        // kernel 57.3 ms; direct with four preloads 55.8 ms (without the
-        // evict-last hint 56.3 ms); three for the pair step 55.2 ms; three
-        // everywhere 55.7; five at 40 registers 55.4; with 128-row CTAs
-        // 54.7 ms, and five for the plain SpMV step 53.4 ms)
+        // matrix in L2: entries preloaded before the dependency wait -- four
+        // at 32 registers (2048 threads per SM), five for the plain SpMV step
+        // (still 32), five at 40 registers (1536 threads) for the second step
+        // of a pair of Algorithm 1, which spills at 32 (2-D 1000^2 FP64
+        // chains: staged kernel 57.3 ms; direct with four preloads 55.8 ms
+        // (without the evict-last hint 56.3 ms); three for the pair step at
+        // 32 registers 55.2 ms; with 128-row CTAs 54.7 ms; five for the plain
+        // SpMV step 53.4 ms; five for the pair step at 40 registers 52.5 ms,
+        // four there 52.8 ms)
         cudaError_t ed;
         if (small) {
             // 64-row CTAs (the residual keeps 256: one partial sum per 256
@@ -751,8 +753,8 @@ int32_t launch_step(int op, const StepArgs<T>& a_in, cudaStream_t s) {
                 cfg.gridDim = dim3((unsigned)(((int64_t)a_in.n + DIRECT_L2_ROWS - 1) /
                                               DIRECT_L2_ROWS));
             }
-            if (op == OP_PHI_PAIR2)
-                ed = launch_direct<T, 3, 8, true>(cfg, op, a);
+            if (op == OP_PHI_PAIR2)   // five entries at 40 registers
+                ed = launch_direct<T, 5, 6, true>(cfg, op, a);
             else if (op == OP_SPMV)   // five entries: a 5-point row whole
                 ed = launch_direct<T, 5, 8, true>(cfg, op, a);
             else
